@@ -1,0 +1,96 @@
+"""The oracle against facts the paper and the mathematics fix (CPU only)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0909_2000_gb300 import synth
+from tests import pins
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def c_plot(x, y, w, match, mismatch):
+    return oracle.plot(x, y, w, match, mismatch, nthreads=3)
+
+
+def py_plot(x, y, w, match, mismatch):
+    return oracle.plot_py(x, y, w, match, mismatch)
+
+
+def test_battery_c_oracle():
+    assert pins.pin_battery(c_plot) == []
+
+
+def test_battery_python_oracle():
+    assert pins.pin_battery(py_plot) == []
+
+
+def test_c_and_python_oracles_agree():
+    for seed, (m, n, w, sc) in enumerate([(30, 27, 7, (1, 0)), (25, 31, 9, (2, 1)), (40, 12, 11, (1, 0))]):
+        x = synth.dna(seed, 1, m)
+        y = synth.dna(seed, 2, n)
+        assert np.array_equal(c_plot(x, y, w, *sc), py_plot(x, y, w, *sc))
+
+
+def test_thread_count_does_not_matter():
+    x, y = synth.protein(3, 1, 90), synth.protein(3, 2, 70)
+    a = oracle.plot(x, y, 13, 2, 1, nthreads=1)
+    b = oracle.plot(x, y, 13, 2, 1, nthreads=7)
+    assert np.array_equal(a, b)
+
+
+def test_samples_match_full_plot():
+    x, y = synth.dna(4, 1, 120), synth.dna(4, 2, 101)
+    full = oracle.plot(x, y, 17)
+    ii = synth.below(4, 3, 500, full.shape[0])
+    jj = synth.below(4, 4, 500, full.shape[1])
+    assert np.array_equal(oracle.samples(x, y, 17, ii, jj), full[ii, jj])
+    with pytest.raises(ValueError):
+        oracle.samples(x, y, 17, [full.shape[0]], [0])
+
+
+def test_all_byte_values_are_symbols():
+    # equality is byte equality: 0x00 and 0xFF are ordinary characters
+    x = np.arange(256, dtype=np.uint8)
+    y = np.arange(256, dtype=np.uint8)[::-1].copy()
+    p = oracle.plot(np.concatenate([x, x]), np.concatenate([x, y]), 8)
+    assert p[0, 0] == 8 and p[3, 3] == 8          # identical windows
+    assert p[0, 300] == 1 or p[0, 300] == 0
+
+
+def test_dollar_golden():
+    # Section 2 prints the example abab -> $a$b$a$b
+    with open(os.path.join(HERE, "golden", "dollar_interleave.txt")) as f:
+        lines = [l.split("#")[0].strip() for l in f if l.split("#")[0].strip()]
+    src, dst = lines[0].split()
+    assert pins.dollar_interleave(src.encode()).decode() == dst
+
+
+def test_plot_512_golden():
+    """The 496 x 496 LCS plot of uniform DNA (m = n = 512, w = 16, seed 0),
+    against the checksum and histogram stored by tests/golden/make_golden.py."""
+    c = synth.dna_plot_512(0)
+    p = oracle.plot(c.x, c.y, c.w)
+    gold = dict(l.split("=", 1) for l in open(os.path.join(HERE, "golden", "lcs_dna_512_w16.txt")).read().split()
+                if "=" in l)
+    assert p.shape == (496, 496)
+    assert oracle.checksum(p) == int(gold["checksum"])
+    assert oracle.histogram(p, c.w + 1).tolist() == [int(v) for v in gold["histogram"].split(",")]
+
+
+def test_chvatal_sankoff_sanity():
+    # not a pin: the mean LCS fraction of random DNA windows of length 64 sits
+    # a little below the sigma = 4 Chvatal-Sankoff constant (about 0.654)
+    x, y = synth.dna(11, 1, 400), synth.dna(11, 2, 400)
+    p = oracle.plot(x, y, 64)
+    assert 0.55 < p.mean() / 64 < 0.66
+
+
+def test_checksum_bands_add_up():
+    x, y = synth.dna(12, 1, 60), synth.dna(12, 2, 50)
+    p = oracle.plot(x, y, 9)
+    total = oracle.checksum(p)
+    parts = (oracle.checksum(p[:20], 0) + oracle.checksum(p[20:], 20)) % (1 << 64)
+    assert total == parts
