@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark: window-pair cells per second of the GB300 alignment-plot path.
+
+Default workload (one step = the whole hot path over one input):
+    LCS alignment plot of DNA, m = n = 100,000, w = 100, with 20 planted
+    homologous segments (2000 long, 10% substitutions, 5% indels): the full
+    99,900 x 99,900 uint8 plot in HBM, then the dots with WLCS >= 80 from it.
+
+metric  = m * n * w / step time (window-pair cells/s), whole job.
+roofline: the strip-comb kernel is bound by the integer ALU.  Its algorithmic
+    work is 6 lane-operations per comb cell (Section 3's vector step: match
+    mask, compare/exchange as min and max, two blends, the per-column
+    increment), i.e. 1.5 32-bit operations per cell with 4 lanes per
+    register.  Comb cells per plot = (m - w)(n - 1)w.  The peak is
+    SMs x 32-bit integer lanes per SM per clock x the SM clock.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank combs its own copy of the workload (independent
+problems, no collective on the data path; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+INT32_LANES_PER_SM_CLK = 128      # 32-bit integer lanes per SM per clock (GB300)
+SM_MAX_MHZ = 2070.0               # maximum SM clock of a GB300
+ALG_OPS_PER_CELL = 6.0 / 4.0      # 6 lane-ops per cell, 4 lanes per 32-bit op
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lcs_dna_100k_w100",
+                    choices=["lcs_dna_100k_w100", "lcs_dna_512_w16", "score_protein_20k_w64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_0909_2000_gb300 import synth
+    if name == "lcs_dna_100k_w100":
+        return synth.dna_plot_100k(0)
+    if name == "lcs_dna_512_w16":
+        return synth.dna_plot_512(0)
+    return synth.protein_score_20k(0)
+
+
+def describe(c):
+    rows, cols = len(c.x) - c.w, len(c.y) - c.w
+    score = tuple(c.scores[:2]) == (2, 1)
+    return {
+        "workload": c.name, "m": len(c.x), "n": len(c.y), "w": c.w,
+        "scores": "match 2, mismatch 1, gap 0" if score else "LCS (match 1, mismatch 0, gap 0)",
+        "output": "full %dx%d %s plot in HBM%s" % (rows, cols, "uint16" if score else "uint8",
+                                                  "" if c.threshold is None else
+                                                  " + row-major dots >= %d" % c.threshold),
+        "inputs": "seeded synthetic (SplitMix64), resident in HBM",
+        "l2": "output %.2f GB per step >> 129 MB L2; L2 flushed (256 MB write) before every timed step"
+              % (rows * cols * (2 if score else 1) / 1e9),
+    }
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(c, seconds, seed=7):
+    """Times the oracle on seeded window pairs of the workload, scaled so the
+    run takes about ``seconds``; returns (cells/s, pairs, elapsed, threads)."""
+    import oracle
+    from paper_0909_2000_gb300 import synth
+    rows, cols = len(c.x) - c.w, len(c.y) - c.w
+    nth = cores()
+    match, mismatch = c.scores[0], c.scores[1]
+
+    def run(k, off):
+        ii = synth.below(seed, 1, k, rows, off)
+        jj = synth.below(seed, 2, k, cols, off)
+        t = time.perf_counter()
+        oracle.samples(c.x, c.y, c.w, ii, jj, match, mismatch, nthreads=nth)
+        return time.perf_counter() - t
+
+    k = 256 * nth
+    dt = run(k, 0)
+    while dt < 0.5:
+        k *= 4
+        dt = run(k, 0)
+    k2 = max(k, int(k * seconds / max(dt, 1e-6) * 0.9))
+    dt2 = run(k2, k)
+    return k2 * c.w / dt2, k2, dt2, nth
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons = [], [], set()
+        for line in self.file.read().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                  "sw_power_cap"], f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.file.name)
+        if not sm:
+            return None
+        busy = sorted(sm)[len(sm) // 4:] or sm     # drop idle samples at the edges
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def profile_traffic(kernel_tag):
+    """dram bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel_tag)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    from paper_0909_2000_gb300 import build as b
+    if rec.get("sources") != b.kernel_digest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    c = workload(args.workload)
+    per = max(2.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    rates = []
+    for s in range(args.warmup + args.steps):
+        r, k, dt, nth = oracle_rate(c, per, seed=100 + s)
+        if s >= args.warmup:
+            rates.append((r, k, dt))
+    v = statistics.median([r for r, _, _ in rates])
+    line = {
+        "impl": "reference", "metric": "window-pair cells/sec (m*n*w/s)", "value": v,
+        "unit": "cells/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": describe(c),
+        "cpu_baseline": {"value": v, "unit": "cells/s", "cores": cores(), "kind": "oracle",
+                         "cpu": cpu_model(),
+                         "sample": "%d seeded window pairs per step (O(w^2) DP each), all host cores"
+                                   % rates[0][1]},
+        "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_0909_2000_gb300 as ap
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    ap.load(build_if_missing=True)
+    c = workload(args.workload)
+    dev = torch.device("cuda", local)
+    m, n, w = len(c.x), len(c.y), c.w
+    score = tuple(c.scores[:2]) == (2, 1)
+    scores = ap.SCORE if score else ap.LCS
+    rows, cols = ap.plot_shape(m, n, w)
+    plan = ap.plot_plan(m, n, w, scores)
+    x = torch.from_numpy(c.x).to(dev)
+    y = torch.from_numpy(c.y).to(dev)
+    out = torch.empty((rows, cols), dtype=torch.int16 if score else torch.uint8, device=dev)
+    thr = c.threshold
+    ws = torch.empty(max(ap.plot_dots_workspace_size(rows), 1), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # size the dot buffer once (counting pass), outside the timed region
+    ap.alignment_plot(x, y, w, scores, out=out)
+    dots = None
+    ndots = 0
+    if thr is not None:
+        _, ndots = ap.plot_dots(out, thr, workspace=ws)
+        dots = torch.empty((max(ndots, 1), 3), dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+
+    launches_per_step = 1 + (3 if thr is not None else 0)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        ap.alignment_plot(x, y, w, scores, out=out)
+        if ev:
+            ev[1].record(stream)
+        if thr is not None:
+            ap.plot_dots(out, thr, dots=dots, workspace=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    if rank == 0:
+        clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    step_ms, comb_ms = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)                      # evict L2 (outside the events)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        step((e[0], e[1]))
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        comb_ms.append(e[0].elapsed_time(e[1]))
+        step_ms.append(e[0].elapsed_time(e[2]))
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop() if rank == 0 else None
+
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    logical = float(m) * n * w
+    value = logical * world * args.steps / (total_ms / 1e3)
+
+    # parity spot-check of this run's output against the oracle (outside timing)
+    import oracle
+    from paper_0909_2000_gb300 import synth
+    ii = synth.below(11, 1, 2000, rows)
+    jj = synth.below(11, 2, 2000, cols)
+    got = out.cpu().numpy()[ii, jj].astype(np.int64) if rows * cols < (1 << 28) else \
+        out[torch.from_numpy(ii).to(dev), torch.from_numpy(jj).to(dev)].cpu().numpy().astype(np.int64)
+    want = oracle.samples(c.x, c.y, w, ii, jj, c.scores[0], c.scores[1])
+    parity_ok = bool(np.array_equal(got, want))
+
+    # roofline of the comb kernel (integer ALU)
+    comb_cells = float(rows) * (n - 1) * (2 * w if score else w) * (2 if score else 1)
+    alg_ops = comb_cells * ALG_OPS_PER_CELL
+    comb_s = statistics.mean(comb_ms) / 1e3
+    achieved = alg_ops / comb_s / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak = sms * INT32_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = profile_traffic("comb/" + c.name)
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = measure_e2e(ap, c, scores, thr, dev, min(args.steps, 3))
+
+    line = {
+        "metric": "window-pair cells/sec (m*n*w/s)",
+        "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8" if not score else "u8 keys, u16 out",
+        "data": "synthetic", "config": describe(c),
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "comb_kernel (strip comb), %d launch per step" % 1,
+                     "peak_basis": "%d SMs x %d int32 lanes/clk x %.0f MHz (max SM clock)"
+                                   % (sms, INT32_LANES_PER_SM_CLK, SM_MAX_MHZ),
+                     "comb_ms": statistics.mean(comb_ms),
+                     "frac_at_measured_clock": (achieved / (sms * INT32_LANES_PER_SM_CLK *
+                                                            clk["sm_mhz"] * 1e6 / 1e12)
+                                                if clk else None)},
+        "plan": plan,
+        "physical_cells_per_s": plan["physical_cells"] / comb_s,
+        "dots": ndots,
+        "parity_samples_ok": parity_ok,
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, k, dt, nth = oracle_rate(c, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": r, "unit": "cells/s", "cores": nth, "kind": "oracle",
+                                "cpu": cpu_model(),
+                                "sample": "%d seeded window pairs of this workload, O(w^2) DP each, "
+                                          "%.1f s on %d host threads" % (k, dt, nth)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_e2e(ap, c, scores, thr, dev, steps):
+    """Same metric through the public API from pinned host memory: copy x, y
+    in, comb, copy the plot (and dots) back, every step."""
+    import torch
+    m, n, w = len(c.x), len(c.y), c.w
+    rows, cols = ap.plot_shape(m, n, w)
+    score = scores == ap.SCORE
+    hx = torch.from_numpy(c.x).pin_memory()
+    hy = torch.from_numpy(c.y).pin_memory()
+    dt = torch.int16 if score else torch.uint8
+    hout = torch.empty((rows, cols), dtype=dt, pin_memory=True)
+    dx = torch.empty(m, dtype=torch.uint8, device=dev)
+    dy = torch.empty(n, dtype=torch.uint8, device=dev)
+    dout = torch.empty((rows, cols), dtype=dt, device=dev)
+    ws = torch.empty(max(ap.plot_dots_workspace_size(rows), 1), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    nd_bytes = 0
+
+    def one():
+        nonlocal nd_bytes
+        dx.copy_(hx, non_blocking=True)
+        dy.copy_(hy, non_blocking=True)
+        ap.alignment_plot(dx, dy, w, scores, out=dout)
+        if thr is not None:
+            d, cnt = ap.plot_dots(dout, thr, workspace=ws)
+            hd = d[:cnt].cpu()
+            nd_bytes = cnt * 12
+        hout.copy_(dout, non_blocking=True)
+        torch.cuda.synchronize()
+
+    one()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    return {"value": float(m) * n * w / t, "unit": "cells/s", "h2d_bytes_per_step": m + n,
+            "d2h_bytes_per_step": rows * cols * hout.element_size() + nd_bytes + 8,
+            "ms_per_step": t * 1e3, "steps": steps}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * alnplot.h -- C ABI of the GB300 alignment-plot library (libalnplot.so).
+ *
+ * An alignment plot (Krusche & Tiskin, "Computing alignment plots
+ * efficiently", Section 2) holds, for two strings x (length m) and y
+ * (length n) and a window length w, one value per pair of w-windows:
+ *
+ *     P[i][j] = best alignment score of x[i .. i+w) and y[j .. j+w)
+ *     for 0 <= i < m - w and 0 <= j < n - w
+ *
+ * This is the paper's index range {1..m-w} x {1..n-w}, written 0-based.
+ * The library computes every value with the seaweed strip sweep of
+ * Theorem 3.1 and Section 3, at O(w) per column per strip.  It does not
+ * run the O(w^2) dynamic programme once per window pair.
+ *
+ * Conventions shared by every call:
+ *   - Sequences are arrays of bytes; two characters match when their bytes
+ *     are equal, so all 256 byte values are ordinary characters.
+ *   - Pointers named "device" are CUDA device pointers owned by the caller;
+ *     "host" pointers are ordinary host memory.  The library never frees
+ *     caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream are stream-ordered: they enqueue
+ *     work and return without waiting, unless stated otherwise.
+ *   - Every call returns an ap_status and never aborts.  On failure,
+ *     ap_last_error() gives a message for the calling thread.
+ */
+#ifndef ALNPLOT_H
+#define ALNPLOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ap_status {
+    AP_OK = 0,
+    AP_E_INVAL = 1,        /* bad argument (null pointer, w < 1, ld too small, ...) */
+    AP_E_UNSUPPORTED = 2,  /* valid request that this build does not handle */
+    AP_E_NOMEM = 3,        /* workspace or budget too small */
+    AP_E_OVERFLOW = 4,     /* more dots than the caller's buffer holds */
+    AP_E_CUDA = 5,         /* a CUDA runtime call failed */
+    AP_E_TIMEOUT = 6,      /* a wait reached its time limit */
+    AP_E_BUSY = 7,         /* no free slot right now */
+    AP_E_CANCELLED = 8     /* the job was cancelled */
+} ap_status;
+
+/*
+ * Alignment scores, normalised so that gap = 0 and 0 <= mismatch < match
+ * (Section 2: "LCS corresponds to match 1, mismatch 0, gap 0").  Supported:
+ *   {1, 0, 0}  LCS: P = LLCS of the two windows, 0 <= P <= w.
+ *   {2, 1, 0}  Section 2's scheme (match 1, mismatch 0, gap -1/2), shifted
+ *              so gaps score 0 and doubled: P = T = S + w, w <= T <= 2w,
+ *              where S is the (1, 0, -1/2) score.  Computed as the LCS of the
+ *              '$'-interleaved windows (Section 2), with Definition 3.2's
+ *              (w, 2) restriction.
+ * Any scheme (a, b, g) with g < 0 maps to {a - 2g, b - 2g, 0} after scaling
+ * to integers; other normalised pairs return AP_E_UNSUPPORTED.
+ */
+typedef struct ap_scores {
+    int32_t match;
+    int32_t mismatch;
+    int32_t gap;
+} ap_scores;
+
+/* One dot of a thresholded plot (Section 1: a dot for each window pair whose
+ * score passes the threshold).  value = P[i][j]. */
+typedef struct ap_dot {
+    uint32_t i;
+    uint32_t j;
+    uint16_t value;
+    uint16_t pad;
+} ap_dot;
+
+/* How a plot call is carried out (kernel variant and tiling); informational. */
+typedef struct ap_plan {
+    int32_t lane_bits;        /* 8 or 16: bits per seaweed key lane */
+    int32_t strips_per_reg;   /* strips held side by side in one 32-bit register */
+    int32_t rows_per_lane;    /* comb rows each thread holds (compile-time) */
+    int32_t lanes_per_strip;  /* threads that split one strip's rows */
+    int32_t comb_rows;        /* physical comb height: w (LCS) or 2w (score) */
+    int32_t chunk;            /* plot columns per tile */
+    int64_t tiles;            /* strip groups x column chunks */
+    int64_t physical_cells;   /* comb cell updates, warm-up and padding included */
+    int64_t logical_cells;    /* (m - w)(n - w) w: window pairs times window length */
+} ap_plan;
+
+/* Library version string. */
+const char *ap_version(void);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char *ap_last_error(void);
+
+/* Name of a status code. */
+const char *ap_status_string(ap_status s);
+
+/*
+ * Plot shape (Section 2): rows = max(0, m - w), cols = max(0, n - w).
+ * rows, cols: host pointers, written on success.  AP_E_INVAL if w < 1,
+ * m < 0, n < 0 or a pointer is null.
+ */
+ap_status ap_plot_shape(int64_t m, int64_t n, int32_t w, int64_t *rows,
+                        int64_t *cols);
+
+/*
+ * The plan ap_alignment_plot would use for these sizes (host only, no GPU
+ * work).  `plan`: host pointer, written on success.
+ */
+ap_status ap_plot_plan(int64_t m, int64_t n, int32_t w,
+                       const ap_scores *scores, ap_plan *plan);
+
+/*
+ * Tuning: force the number of plot columns per tile (rounded up to a
+ * multiple of 32) for later plot and dots calls in this process; 0 restores
+ * the automatic choice.  Results do not depend on it (a tile starting at
+ * column c0 combs w - 1 warm-up columns, which is exact; Theorem 3.1 applied
+ * to the substring of y from c0).  Process-wide; AP_E_INVAL if chunk < 0.
+ */
+ap_status ap_set_chunk(int64_t chunk);
+
+/*
+ * Full alignment plot (Section 2 definition; Theorem 3.1 / Section 3 method).
+ *
+ *   x       device, m bytes          y       device, n bytes
+ *   w       window length, >= 1
+ *   scores  host, {1,0,0} or {2,1,0} (see ap_scores)
+ *   out     device, rows x ld elements, row-major; out[i*ld + j] = P[i][j]
+ *   out_elem_bytes  1 (uint8) or 2 (uint16)
+ *   ld      elements between consecutive rows, ld >= cols
+ *   stream  cudaStream_t as void*
+ *
+ * Errors: AP_E_INVAL for null pointers, w < 1, ld < cols, an element size
+ * other than 1 or 2, or uint8 output when the largest possible value
+ * (w for LCS, 2w for {2,1,0}) exceeds 255; AP_E_UNSUPPORTED for other
+ * score schemes or w beyond the largest compiled comb height;
+ * AP_E_CUDA if a launch fails.  If m <= w or n <= w the plot is empty:
+ * nothing is written and AP_OK is returned.  Stream-ordered; allocates no
+ * device memory.
+ */
+ap_status ap_alignment_plot(const uint8_t *x, int64_t m, const uint8_t *y,
+                            int64_t n, int32_t w, const ap_scores *scores,
+                            void *out, int32_t out_elem_bytes, int64_t ld,
+                            void *stream);
+
+/*
+ * Bytes of device workspace ap_alignment_dots needs for these sizes.
+ * bytes: host pointer, written on success.
+ */
+ap_status ap_dots_workspace_size(int64_t m, int64_t n, int32_t w,
+                                 const ap_scores *scores, int64_t *bytes);
+
+/*
+ * Thresholded plot: every window pair with P[i][j] >= threshold, as ap_dot
+ * records in row-major order (i, then j) -- Section 1's dot plot, with the
+ * inclusive threshold on the alignment score.
+ *
+ *   dots       device, room for `cap` records (may be null when cap = 0)
+ *   count      host; receives the total number of qualifying pairs, also
+ *              when it exceeds cap
+ *   workspace  device, >= ap_dots_workspace_size(...) bytes, caller-owned
+ *
+ * The plot is computed band by band into the workspace, so no full-size
+ * plot is ever allocated.  Returns AP_E_OVERFLOW (after writing the first
+ * `cap` dots and the full count) when count > cap.  Synchronises `stream`
+ * before returning, because the status depends on the count.
+ */
+ap_status ap_alignment_dots(const uint8_t *x, int64_t m, const uint8_t *y,
+                            int64_t n, int32_t w, const ap_scores *scores,
+                            int32_t threshold, ap_dot *dots, int64_t cap,
+                            int64_t *count, void *workspace,
+                            int64_t workspace_bytes, void *stream);
+
+/*
+ * Dots of an existing plot in device memory (same order and overflow rule
+ * as ap_alignment_dots).  plot: device, rows x ld elements of elem_bytes
+ * (1 or 2).  Workspace: device, >= ap_plot_dots_workspace_size(rows) bytes.
+ * Synchronises `stream` before returning.
+ */
+ap_status ap_plot_dots_workspace_size(int64_t rows, int64_t *bytes);
+ap_status ap_plot_dots(const void *plot, int32_t elem_bytes, int64_t rows,
+                       int64_t cols, int64_t ld, int32_t threshold,
+                       ap_dot *dots, int64_t cap, int64_t *count,
+                       void *workspace, int64_t workspace_bytes, void *stream);
+
+/*
+ * Checksum and value histogram of a plot in device memory, for checking
+ * large plots without copying them:
+ *   sum over cells of P[i][j] * (i*2654435761 + j*40503 + 1)  mod 2^64
+ * and hist[v] = number of cells with value v, for v < nbins (larger values
+ * are not counted).  result: device, 1 + nbins uint64 words (checksum first),
+ * overwritten.  Stream-ordered.
+ */
+ap_status ap_plot_checksum(const void *plot, int32_t elem_bytes, int64_t rows,
+                           int64_t cols, int64_t ld, int32_t nbins,
+                           uint64_t *result, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALNPLOT_H */

@@ -1,1 +1,280 @@
-"""GB300-native alignment plots (Krusche & Tiskin, arXiv 0909.2000)."""
+"""GB300-native alignment plots (Krusche & Tiskin, arXiv 0909.2000).
+
+A thin ctypes binding over ``libalnplot.so``, whose C ABI is declared in
+``include/alnplot.h``.  The functions here only marshal arguments; all
+computation runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  Nothing here falls back to the CPU: if the library
+cannot be loaded, every call raises.
+
+    import torch, paper_0909_2000_gb300 as ap
+    x = torch.tensor(list(b"ACGT..."), dtype=torch.uint8, device="cuda")
+    plot = ap.alignment_plot(x, y, w=100)              # (m-w, n-w) uint8
+    dots, count = ap.alignment_dots(x, y, w=100, threshold=80)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "load", "ApError", "LCS", "SCORE", "plot_shape", "plot_plan", "alignment_plot",
+    "alignment_dots", "plot_dots", "plot_checksum", "version", "set_chunk", "DOT_DTYPE_FIELDS",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lock = threading.Lock()
+_lib = None
+
+LCS = (1, 0, 0)
+SCORE = (2, 1, 0)
+
+AP_OK, AP_E_INVAL, AP_E_UNSUPPORTED, AP_E_NOMEM, AP_E_OVERFLOW = 0, 1, 2, 3, 4
+AP_E_CUDA, AP_E_TIMEOUT, AP_E_BUSY, AP_E_CANCELLED = 5, 6, 7, 8
+STATUS_NAMES = {0: "AP_OK", 1: "AP_E_INVAL", 2: "AP_E_UNSUPPORTED", 3: "AP_E_NOMEM",
+                4: "AP_E_OVERFLOW", 5: "AP_E_CUDA", 6: "AP_E_TIMEOUT", 7: "AP_E_BUSY",
+                8: "AP_E_CANCELLED"}
+DOT_DTYPE_FIELDS = [("i", "<u4"), ("j", "<u4"), ("value", "<u2"), ("pad", "<u2")]
+
+
+class ApError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class ap_scores(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32), ("gap", ctypes.c_int32)]
+
+
+class ap_plan(ctypes.Structure):
+    _fields_ = [("lane_bits", ctypes.c_int32), ("strips_per_reg", ctypes.c_int32),
+                ("rows_per_lane", ctypes.c_int32), ("lanes_per_strip", ctypes.c_int32),
+                ("comb_rows", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("tiles", ctypes.c_int64), ("physical_cells", ctypes.c_int64),
+                ("logical_cells", ctypes.c_int64)]
+
+
+def _declare(lib):
+    i32, i64, p, u64p = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    sc = ctypes.POINTER(ap_scores)
+    lib.ap_version.restype = ctypes.c_char_p
+    lib.ap_last_error.restype = ctypes.c_char_p
+    lib.ap_status_string.restype = ctypes.c_char_p
+    lib.ap_status_string.argtypes = [ctypes.c_int]
+    sigs = {
+        "ap_set_chunk": [i64],
+        "ap_plot_shape": [i64, i64, i32, i64p, i64p],
+        "ap_plot_plan": [i64, i64, i32, sc, ctypes.POINTER(ap_plan)],
+        "ap_alignment_plot": [p, i64, p, i64, i32, sc, p, i32, i64, p],
+        "ap_dots_workspace_size": [i64, i64, i32, sc, i64p],
+        "ap_alignment_dots": [p, i64, p, i64, i32, sc, i32, p, i64, i64p, p, i64, p],
+        "ap_plot_dots_workspace_size": [i64, i64p],
+        "ap_plot_dots": [p, i32, i64, i64, i64, i32, p, i64, i64p, p, i64, p],
+        "ap_plot_checksum": [p, i32, i64, i64, i64, i32, u64p, p],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        fn.argtypes = args
+    return lib
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libalnplot.so")
+
+
+def load(build_if_missing: bool = True):
+    """Load libalnplot.so (building it with nvcc first if it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if build_if_missing:
+                from . import build as _build
+                path = _build.build()
+            if not os.path.exists(path):
+                raise ApError(AP_E_CUDA, "libalnplot.so is missing; run the build")
+            _lib = _declare(ctypes.CDLL(path))
+    return _lib
+
+
+def version() -> str:
+    return load().ap_version().decode()
+
+
+def _check(status: int, allow=()):
+    if status != AP_OK and status not in allow:
+        raise ApError(status, load().ap_last_error().decode())
+    return status
+
+
+def _scores(scores) -> ap_scores:
+    s = tuple(scores) if scores is not None else LCS
+    if len(s) == 2:
+        s = (s[0], s[1], 0)
+    return ap_scores(int(s[0]), int(s[1]), int(s[2]))
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _dev_u8(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if t.dtype != torch.uint8 or not t.is_cuda or t.dim() != 1 or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous 1-D uint8 CUDA tensor" % name)
+    return t
+
+
+def set_chunk(chunk: int) -> None:
+    """Force plot columns per tile (0 = automatic); results do not change."""
+    _check(load().ap_set_chunk(int(chunk)))
+
+
+def plot_shape(m: int, n: int, w: int) -> tuple[int, int]:
+    r, c = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().ap_plot_shape(m, n, w, ctypes.byref(r), ctypes.byref(c)))
+    return r.value, c.value
+
+
+def plot_plan(m: int, n: int, w: int, scores=LCS) -> dict:
+    pl = ap_plan()
+    sc = _scores(scores)
+    _check(load().ap_plot_plan(m, n, w, ctypes.byref(sc), ctypes.byref(pl)))
+    return {f: getattr(pl, f) for f, _ in ap_plan._fields_}
+
+
+def alignment_plot(x, y, w: int, scores=LCS, out=None, out_dtype=None, stream=None):
+    """Full plot P[i, j] for 0 <= i < m-w, 0 <= j < n-w (uint8 or uint16).
+
+    ``out`` may be a preallocated 2-D CUDA tensor (rows x ld, ld >= cols, or a
+    wider view); otherwise one is allocated.  Stream-ordered on ``stream``."""
+    import torch
+    x, y = _dev_u8(x, "x"), _dev_u8(y, "y")
+    rows, cols = plot_shape(x.numel(), y.numel(), w)
+    sc = _scores(scores)
+    if out is None:
+        if out_dtype is None:
+            vmax = 2 * w if sc.match == 2 else w
+            out_dtype = torch.uint8 if vmax <= 255 else torch.int16
+        out = torch.empty((rows, cols), dtype=out_dtype, device=x.device)
+    if out.element_size() not in (1, 2) or not out.is_cuda:
+        raise ValueError("out must be a CUDA tensor of 8- or 16-bit elements")
+    if out.dim() != 2 or out.stride(1) != 1 or out.shape[0] < rows or out.shape[1] < cols:
+        raise ValueError("out must be a row-major 2-D tensor of at least %d x %d" % (rows, cols))
+    ld = out.stride(0) if rows > 1 else max(cols, out.shape[1])
+    _check(load().ap_alignment_plot(ctypes.c_void_p(x.data_ptr()), x.numel(),
+                                    ctypes.c_void_p(y.data_ptr()), y.numel(), w,
+                                    ctypes.byref(sc), ctypes.c_void_p(out.data_ptr()),
+                                    out.element_size(), ld, _stream_handle(stream)))
+    return out
+
+
+def _dots_tensor(count: int, device):
+    import torch
+    return torch.empty((max(count, 1), 3), dtype=torch.int32, device=device)
+
+
+def dots_to_numpy(dots, count: int):
+    """(count, 3) int64 array of (i, j, value) from a raw ap_dot buffer."""
+    import numpy as np
+    raw = dots[:count].cpu().numpy().view(np.uint32)
+    out = np.zeros((count, 3), dtype=np.int64)
+    out[:, 0] = raw[:, 0]
+    out[:, 1] = raw[:, 1]
+    out[:, 2] = raw[:, 2] & 0xFFFF
+    return out
+
+
+def alignment_dots(x, y, w: int, threshold: int, scores=LCS, cap: int | None = None,
+                   dots=None, workspace=None, stream=None):
+    """Dots (i, j, value) with P[i, j] >= threshold, row-major.
+
+    Returns (dots, count): ``dots`` is a CUDA int32 tensor of shape (cap, 3)
+    holding ap_dot records (i, j, value | pad << 16); ``count`` is the total
+    number of qualifying pairs.  Raises ApError(AP_E_OVERFLOW) only if
+    ``cap`` was given and is too small; with cap=None the buffer is sized by a
+    counting pass first."""
+    import torch
+    x, y = _dev_u8(x, "x"), _dev_u8(y, "y")
+    lib = load()
+    sc = _scores(scores)
+    need = ctypes.c_int64()
+    _check(lib.ap_dots_workspace_size(x.numel(), y.numel(), w, ctypes.byref(sc), ctypes.byref(need)))
+    if workspace is None:
+        workspace = torch.empty(max(need.value, 1), dtype=torch.uint8, device=x.device)
+    cnt = ctypes.c_int64()
+    st = _stream_handle(stream)
+
+    def run(buf, capacity, allow):
+        return _check(lib.ap_alignment_dots(
+            ctypes.c_void_p(x.data_ptr()), x.numel(), ctypes.c_void_p(y.data_ptr()), y.numel(), w,
+            ctypes.byref(sc), int(threshold),
+            ctypes.c_void_p(buf.data_ptr() if buf is not None else 0), capacity,
+            ctypes.byref(cnt), ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), st), allow)
+
+    if cap is None and dots is None:
+        run(None, 0, (AP_E_OVERFLOW,))
+        dots = _dots_tensor(cnt.value, x.device)
+        run(dots, cnt.value, ())
+        return dots, cnt.value
+    if dots is None:
+        dots = _dots_tensor(cap, x.device)
+    run(dots, dots.shape[0] if cap is None else cap, ())
+    return dots, cnt.value
+
+
+def plot_dots_workspace_size(rows: int) -> int:
+    need = ctypes.c_int64()
+    _check(load().ap_plot_dots_workspace_size(rows, ctypes.byref(need)))
+    return need.value
+
+
+def plot_dots(plot, threshold: int, cap: int | None = None, dots=None, workspace=None,
+              stream=None):
+    """Dots of an existing device plot (same order and overflow rule as
+    alignment_dots).  Returns (dots, count)."""
+    import torch
+    lib = load()
+    rows, cols = plot.shape
+    if workspace is None:
+        workspace = torch.empty(max(plot_dots_workspace_size(rows), 1), dtype=torch.uint8,
+                                device=plot.device)
+    cnt = ctypes.c_int64()
+    st = _stream_handle(stream)
+
+    def run(buf, capacity, allow):
+        return _check(lib.ap_plot_dots(ctypes.c_void_p(plot.data_ptr()), plot.element_size(), rows,
+                                       cols, plot.stride(0) if rows > 1 else cols, int(threshold),
+                                       ctypes.c_void_p(buf.data_ptr() if buf is not None else 0),
+                                       capacity, ctypes.byref(cnt),
+                                       ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), st),
+                      allow)
+
+    if dots is None:
+        if cap is None:
+            run(None, 0, (AP_E_OVERFLOW,))
+            cap = cnt.value
+        dots = _dots_tensor(cap, plot.device)
+    run(dots, dots.shape[0] if cap is None else cap, ())
+    return dots, cnt.value
+
+
+def plot_checksum(plot, nbins: int, stream=None):
+    """(checksum, histogram[nbins]) of a device plot, computed on the GPU."""
+    import torch
+    rows, cols = plot.shape
+    res = torch.zeros(1 + nbins, dtype=torch.int64, device=plot.device)
+    _check(load().ap_plot_checksum(ctypes.c_void_p(plot.data_ptr()), plot.element_size(), rows, cols,
+                                   plot.stride(0) if rows > 1 else cols, nbins,
+                                   ctypes.cast(ctypes.c_void_p(res.data_ptr()), ctypes.POINTER(ctypes.c_uint64)),
+                                   _stream_handle(stream)))
+    r = res.cpu().numpy().view("uint64")
+    return int(r[0]), r[1:].astype("int64")

@@ -1,0 +1,155 @@
+"""Builds libalnplot.so in-tree for sm_103a with nvcc.
+
+The strip-comb kernel is a template over (lane format, rows per thread,
+threads per strip group, score mode).  The compiled variants are listed in
+VARIANTS.  Their instantiations are generated into a few translation units
+under ``_build/``, and all units compile in parallel.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import hashlib
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libalnplot.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC = os.environ.get("NVCC", "nvcc")
+
+
+def _variants():
+    v = []
+    # LCS, 8-bit keys, one thread per strip group: w <= 120, R = roundup(w, 8)
+    for r in range(8, 121, 8):
+        v.append(("U8Lanes", 8, r, 1, False, 8))
+    # score mode, 8-bit keys: w <= 64 on one thread, w <= 120 on two
+    for rp in range(4, 65, 4):
+        v.append(("U8Lanes", 8, 2 * rp, 1, True, 8))
+    for rp in range(36, 61, 4):
+        v.append(("U8Lanes", 8, 2 * rp, 2, True, 8))
+    # LCS, 16-bit keys, strip rows split over 2, 4 or 8 threads: w <= 512
+    for g in (2, 4, 8):
+        for r in range(16, 65, 8):
+            v.append(("U16Lanes", 16, r, g, False, 8))
+    # score mode, 16-bit keys, 8 threads: w <= 256
+    for rp in range(16, 33, 4):
+        v.append(("U16Lanes", 16, 2 * rp, 8, True, 8))
+    return v
+
+
+VARIANTS = _variants()
+NUNITS = 12   # translation units for the instantiations
+
+
+def _generate() -> list[str]:
+    gen = os.path.join(BUILD, "gen")
+    os.makedirs(gen, exist_ok=True)
+    paths = []
+    parts = [VARIANTS[k::NUNITS] for k in range(NUNITS)]
+    for k, part in enumerate(parts):
+        lines = ['#include "variants.h"', "namespace ap {",
+                 "extern const Variant kVariants%d[];" % k,
+                 "extern const int kNumVariants%d;" % k,
+                 "const Variant kVariants%d[] = {" % k]
+        for (lanes, bits, r, g, score, padr) in part:
+            lines.append("    AP_VARIANT(%s, %d, %d, %d, %s, %d)," % (lanes, bits, r, g,
+                                                                    "true" if score else "false", padr))
+        if not part:
+            lines.append("    {0, 0, 0, false, nullptr},")
+        lines += ["};", "const int kNumVariants%d = %d;" % (k, len(part)), "}  // namespace ap", ""]
+        paths.append(_write_if_changed(os.path.join(gen, "variants_%02d.cu" % k), "\n".join(lines)))
+    table = ['#include <vector>', '#include <mutex>', '#include "variants.h"', "namespace ap {"]
+    for k in range(NUNITS):
+        table.append("extern const Variant kVariants%d[]; extern const int kNumVariants%d;" % (k, k))
+    table += ["const Variant *variant_table(int *count) {",
+              "    static std::vector<Variant> all;",
+              "    static std::once_flag once;",
+              "    std::call_once(once, [] {"]
+    for k in range(NUNITS):
+        table.append("        for (int i = 0; i < kNumVariants%d; ++i) all.push_back(kVariants%d[i]);" % (k, k))
+    table += ["    });", "    *count = (int)all.size();", "    return all.data();", "}",
+              "}  // namespace ap", ""]
+    paths.append(_write_if_changed(os.path.join(gen, "variant_table.cu"), "\n".join(table)))
+    return paths
+
+
+def _write_if_changed(path: str, text: str) -> str:
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
+    return path
+
+
+def _flags():
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                   "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
+
+
+def _deps_digest() -> str:
+    h = hashlib.sha1()
+    for d in (CSRC, INCLUDE):
+        for name in sorted(os.listdir(d)):
+            p = os.path.join(d, name)
+            if os.path.isfile(p):
+                h.update(name.encode())
+                h.update(open(p, "rb").read())
+    h.update(repr(VARIANTS).encode())
+    h.update(repr(_flags()).encode())
+    return h.hexdigest()
+
+
+def kernel_digest() -> str:
+    """Digest of the strip-comb kernel source and variant list (used to tell
+    whether stored profiler counters still describe the current kernel)."""
+    h = hashlib.sha1()
+    h.update(open(os.path.join(CSRC, "comb.cuh"), "rb").read())
+    h.update(repr(VARIANTS).encode())
+    return h.hexdigest()[:16]
+
+
+def _compile(src: str, obj: str, verbose: bool) -> None:
+    cmd = [NVCC] + _flags() + ["-c", src, "-o", obj]
+    if verbose:
+        print(" ".join(cmd), flush=True)
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, r.stdout, r.stderr))
+
+
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
+    """Compile (if sources changed) and return the path of libalnplot.so."""
+    os.makedirs(BUILD, exist_ok=True)
+    stamp = os.path.join(BUILD, "stamp")
+    digest = _deps_digest()
+    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == digest:
+        return LIB
+    if shutil.which(NVCC) is None and not os.path.exists(NVCC):
+        raise RuntimeError("nvcc not found; the CUDA library cannot be built")
+    srcs = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cu")]
+    srcs += _generate()
+    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    jobs = jobs or min(len(srcs), max(1, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        list(ex.map(lambda so: _compile(so[0], so[1], verbose), zip(srcs, objs)))
+    tmp = LIB + ".%d.tmp" % os.getpid()
+    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
+    os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(digest)
+    return LIB
+
+
+if __name__ == "__main__":
+    import time
+    t = time.time()
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print("built in %.1f s" % (time.time() - t))

@@ -1,0 +1,488 @@
+// comb.cuh -- the seaweed strip-comb kernel for alignment plots (sm_103a).
+//
+// Method (Krusche & Tiskin, "Computing alignment plots efficiently"):
+//   * Theorem 3.1: for each x-window (a "strip" of w rows), comb the strip
+//     against all of y, column by column.  One seaweed starts at the top of
+//     every column and one leaves at the bottom.  The LCS of the strip and
+//     the y-window ending at column J is w - d(J).  Here d(J) counts the
+//     seaweeds that started inside the window and have already left at the
+//     bottom inside it.
+//   * Section 2 cell rule: the seaweeds entering a cell from the left (h)
+//     and from the top (v) swap directions in a match cell, or when they
+//     have crossed before; otherwise they cross.  With seaweeds keyed by
+//     start column (larger = newer), "crossed before" means h is newer than
+//     v.  So the bottom output is h if (match or h >= v), else v.
+//   * Section 3: keys need only O(log w) bits (Proposition 3.4).  A seaweed
+//     older than the window is irrelevant, and all such seaweeds can share
+//     one key.  The vector step is the paper's anti-diagonal
+//     compare/exchange with a match mask and a masked blend.
+//
+// GB300 mapping:
+//   * SWAR: one 32-bit register holds the same comb row of NS strips that
+//     are next to each other (4 x 8-bit keys, or 2 x 16-bit keys).  Strip
+//     i+b, row k reads x[i+b+k], so a row register is a 4-byte window of x.
+//     The match mask of each aligned x word is computed once per column,
+//     and the rows are byte shifts (PRMT) of those masks.
+//   * Keys are start columns, not distances, so columns need no increment.
+//     Every Rr columns all keys drop by Rr, saturating at 0 (0 = "older
+//     than any window").  The new seaweed's key cycles in [w, KMAX].
+//   * Each CTA warp owns one tile: a group of strips times a chunk of plot
+//     columns.  A chunk starting at column c0 starts a fresh comb at c0 and
+//     runs w - 1 warm-up columns.  That is exact for every window starting
+//     at or after c0: seaweeds from before c0 are all older than those
+//     windows.
+//   * d(J) is kept with a ring of "left validly" flags indexed by start
+//     column.  This is an O(1)-per-column stand-in for the paper's min-heap
+//     B, with the same numbers.
+//   * When a strip's rows are split over G lanes, the wavefront is skewed
+//     by one column per lane, and v passes down with a warp shuffle.
+//   * Results are staged in shared memory and written to HBM as
+//     row-contiguous, sector-aligned stores.
+//
+// Score mode ({2,1,0}, Section 2): the comb runs on the '$'-interleaved
+// strings x' = $x0$x1..., y' = $y0$y1...  Rows and columns alternate '$'
+// and a character; '$' matches only '$', so no byte value is reserved.
+// Keys are start *pairs* floor(s/2) (the (w,2)-restricted matrix of
+// Definition 3.2 and Proposition 3.4).  Only windows at even offsets
+// exist, and the value is T = 2w - d.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ap {
+
+constexpr int kWarpsPerBlock = 4;
+constexpr int kOB = 32;   // plot columns staged per flush (one per lane)
+
+struct CombParams {
+    const uint8_t *x;
+    const uint8_t *y;
+    int64_t m, n;
+    int32_t w;          // window length (key window, in units)
+    int32_t renorm;     // steps between key renormalisations
+    int64_t rows, cols; // plot shape
+    int64_t chunk;      // plot columns per tile
+    int64_t nsg;        // strip groups (warps along the plot rows)
+    int64_t ntiles;     // nsg * column chunks
+    int64_t tile0;      // first tile of this launch (for split launches)
+    void *out;
+    int64_t ld;         // elements between plot rows
+    int32_t out_bytes;  // 1 or 2
+    int32_t vec_ok;     // output pointer/ld allow aligned vector stores
+    int32_t ring;       // ring slots (power of two > w)
+};
+
+// ---------------------------------------------------------------------------
+// SWAR lane formats
+// ---------------------------------------------------------------------------
+
+struct U8Lanes {
+    static constexpr int NS = 4;        // strips per register
+    static constexpr int BITS = 8;
+    static constexpr int RPW = 4;       // rows per aligned x word
+    static constexpr int KMAX = 127;    // keys are 7-bit; bit 7 is the compare bit
+    static constexpr uint32_t ONES = 0x01010101u;
+    static constexpr uint32_t MSB = 0x80808080u;
+    static constexpr uint32_t LOW = 0x7F7F7F7Fu;
+    static constexpr uint32_t SIGNREP = 0xBA98u;   // each byte := its sign bit
+    static constexpr uint32_t MASK = 0xFFu;
+};
+
+struct U16Lanes {
+    static constexpr int NS = 2;
+    static constexpr int BITS = 16;
+    static constexpr int RPW = 2;
+    static constexpr int KMAX = 32767;
+    static constexpr uint32_t ONES = 0x00010001u;
+    static constexpr uint32_t MSB = 0x80008000u;
+    static constexpr uint32_t LOW = 0x7FFF7FFFu;
+    static constexpr uint32_t SIGNREP = 0xBB99u;   // each half := its sign bit
+    static constexpr uint32_t MASK = 0xFFFFu;
+};
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
+{
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+    return r;
+}
+
+// Row register for rows r = 1..RPW-1 past an aligned word: the lanes start r
+// characters further into the x stream.
+template <class L>
+__device__ __forceinline__ uint32_t row_shift(uint32_t a, uint32_t b, int r)
+{
+    if (L::BITS == 8) return prmt(a, b, 0x3210u + 0x1111u * (uint32_t)r);
+    return prmt(a, b, 0x5432u);   // r == 1 for 16-bit lanes
+}
+
+// Mismatch flags of one aligned word: lane MSB set iff x != y (any byte
+// values).  ((e & LOW) + LOW) has its MSB set iff the low bits of e are
+// nonzero, and never carries across lanes.  OR-ing e adds the top bit.
+template <class L>
+__device__ __forceinline__ uint32_t mismatch_word(uint32_t xw, uint32_t yb)
+{
+    uint32_t e = xw ^ yb;
+    return ((e & L::LOW) + L::LOW) | e;
+}
+
+// One comb cell on NS strips at once.
+//   h: seaweed entering from the left (stays in the row register),
+//   v: seaweed entering from the top (travels down the column),
+//   nz: lane MSB set iff mismatch, pad: lane MSB set iff the row is padding
+//   (a padding row never matches).
+// Bottom output = h where (match or h >= v), else v; right output = other.
+template <class L>
+__device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t nz, uint32_t pad)
+{
+    uint32_t t = h - v + L::MSB;             // lane MSB: h >= v (no cross-lane carry)
+    uint32_t ms = t | (~nz & ~pad);          // lane MSB: swap
+    uint32_t M = prmt(ms, 0u, L::SIGNREP);   // full-lane swap mask
+    uint32_t vn = (h & M) | (v & ~M);
+    h = h ^ v ^ vn;
+    v = vn;
+}
+
+// Mismatch cell (no match possible): swap iff h >= v.
+template <class L>
+__device__ __forceinline__ void cell_mismatch(uint32_t &h, uint32_t &v)
+{
+    uint32_t t = h - v + L::MSB;
+    uint32_t M = prmt(t, 0u, L::SIGNREP);
+    uint32_t vn = (h & M) | (v & ~M);
+    h = h ^ v ^ vn;
+    v = vn;
+}
+
+// Keys drop by rr, saturating at 0.
+template <class L>
+__device__ __forceinline__ uint32_t renorm_key(uint32_t k, uint32_t rr_bias)
+{
+    uint32_t t = k + rr_bias;                 // lane: k + (half - rr), MSB iff k >= rr
+    uint32_t M = prmt(t, 0u, L::SIGNREP);
+    return t & M & L::LOW;
+}
+
+// ---------------------------------------------------------------------------
+// Output staging flush
+// ---------------------------------------------------------------------------
+//
+// stage[jj * (NGRP + 1) + grp] holds, for staged plot column jj, the NS values
+// of group grp's strips (one per lane).  The warp writes `cnt` columns
+// starting at plot column jbase for its SPW strip rows.  Vector path: 8
+// threads cover one row's 32 columns (4 each), 4 rows per pass, so every
+// store instruction writes whole 32-byte sectors.
+template <class L>
+__device__ __forceinline__ uint32_t lane_of(uint32_t w, int b)
+{
+    return (w >> (L::BITS * b)) & L::MASK;
+}
+
+template <class L, int NGRP>
+__device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t *stage,
+                                            int64_t iw, int64_t jbase, int cnt, int lane)
+{
+    constexpr int NS = L::NS;
+    constexpr int SPW = NGRP * NS;
+    if (p.vec_ok) {
+        const int cb = lane & 7;
+        const int j4 = 4 * cb;
+#pragma unroll 1
+        for (int it = 0; it < SPW / 4; ++it) {
+            const int rw = it * 4 + (lane >> 3);
+            const int64_t i = iw + rw;
+            if (i >= p.rows || j4 >= cnt) continue;
+            const int grp = rw / NS, b = rw % NS;
+            const uint32_t *sp = stage + j4 * (NGRP + 1) + grp;
+            const uint32_t w0 = sp[0], w1 = sp[NGRP + 1], w2 = sp[2 * (NGRP + 1)], w3 = sp[3 * (NGRP + 1)];
+            const int64_t off = i * p.ld + jbase + j4;
+            // byte index of lane b's low byte inside a staged word
+            const uint32_t bb = (uint32_t)(b * (L::BITS / 8));
+            if (p.out_bytes == 1) {
+                const uint32_t sel = bb | ((bb + 4u) << 4);
+                const uint32_t lo = prmt(w0, w1, sel), hi = prmt(w2, w3, sel);
+                const uint32_t word = prmt(lo, hi, 0x5410u);
+                uint8_t *o = (uint8_t *)p.out + off;
+                if (j4 + 4 <= cnt) {
+                    *(uint32_t *)o = word;
+                } else {
+                    for (int t = 0; t < cnt - j4; ++t) o[t] = (uint8_t)(word >> (8 * t));
+                }
+            } else {
+                uint32_t lo, hi;
+                if (L::BITS == 8) {
+                    const uint32_t sel = bb | ((bb + 4u) << 4);
+                    lo = prmt(prmt(w0, w1, sel), 0u, 0x4140u);
+                    hi = prmt(prmt(w2, w3, sel), 0u, 0x4140u);
+                } else {
+                    const uint32_t sel = bb | ((bb + 1u) << 4) | ((bb + 4u) << 8) | ((bb + 5u) << 12);
+                    lo = prmt(w0, w1, sel);
+                    hi = prmt(w2, w3, sel);
+                }
+                uint16_t *o = (uint16_t *)p.out + off;
+                if (j4 + 4 <= cnt) {
+                    *(uint2 *)o = make_uint2(lo, hi);
+                } else {
+                    const uint32_t v4[4] = {lo & 0xFFFFu, lo >> 16, hi & 0xFFFFu, hi >> 16};
+                    for (int t = 0; t < cnt - j4; ++t) o[t] = (uint16_t)v4[t];
+                }
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int rw = 0; rw < SPW; ++rw) {
+            const int64_t i = iw + rw;
+            if (i >= p.rows) break;
+            if (lane < cnt) {
+                const uint32_t v = lane_of<L>(stage[lane * (NGRP + 1) + rw / NS], rw % NS);
+                const int64_t off = i * p.ld + jbase + lane;
+                if (p.out_bytes == 1) ((uint8_t *)p.out)[off] = (uint8_t)v;
+                else ((uint16_t *)p.out)[off] = (uint16_t)v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The kernel
+// ---------------------------------------------------------------------------
+//
+// L      lane format (U8Lanes / U16Lanes)
+// R      physical comb rows held by each thread
+// G      threads per strip group (the strip's rows are split over them)
+// SCORE  false: LCS; true: '$'-interleaved strings ({2,1,0} scores)
+// PADR   trailing rows of each thread that may be padding (never match)
+//
+// Each step combs two physical columns, interleaved row by row, so a thread
+// always has two independent dependency chains:
+//   LCS:   columns 2u and 2u+1 (unit u = two plot columns, keys per column);
+//   score: the '$' column and the character column of y' pair u (keys per pair).
+// Threads of a strip group are skewed by one step: thread g works on unit
+// u = s - g and takes its top seaweeds from thread g-1 by warp shuffle.
+template <class L, int R, int G, bool SCORE, int PADR>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+comb_kernel(CombParams p)
+{
+    constexpr int NS = L::NS;
+    constexpr int NGRP = 32 / G;
+    constexpr int SPW = NGRP * NS;                    // strips per warp
+    constexpr int RP = SCORE ? R / 2 : R;             // x rows per thread
+    constexpr int NQ = RP / L::RPW + 1;               // aligned x words
+    constexpr int PADU = SCORE ? PADR / 2 : PADR;     // padding units (rows or pairs)
+    static_assert(R % (SCORE ? 2 * L::RPW : L::RPW) == 0, "R must fill whole x words");
+    static_assert(PADU <= RP, "padding window larger than the lane");
+
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int g = (G == 1) ? 0 : (lane % G);
+    const int grp = lane / G;
+    const int64_t tile = p.tile0 + (int64_t)blockIdx.x * kWarpsPerBlock + wid;
+    if (tile >= p.ntiles) return;
+
+    uint32_t *ring = smem + wid * (p.ring * NGRP + kOB * (NGRP + 1));
+    uint32_t *stage = ring + p.ring * NGRP;
+
+    const int64_t sg = tile % p.nsg;
+    const int64_t ch = tile / p.nsg;
+    const int64_t iw = sg * SPW;                  // first strip of the warp
+    const int64_t ig = iw + (int64_t)grp * NS;    // first strip of the group
+    const int64_t c0 = ch * p.chunk;
+    const int64_t c1 = (c0 + p.chunk < p.cols) ? c0 + p.chunk : p.cols;
+    const int wk = p.w;                            // window, in key units
+
+    // x rows (LCS) or pairs (score) held by this thread: [ub, ub + nreal).
+    const int ub = (g * wk) / G;
+    const int nreal = ((g + 1) * wk) / G - ub;
+
+    // Aligned x words of this thread's stream x[ig + ub ...].
+    uint32_t xw[NQ];
+    {
+        const int64_t base = ig + ub;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            uint32_t wv = 0;
+#pragma unroll
+            for (int t = 0; t < L::RPW; ++t) {
+                const int64_t idx = base + q * L::RPW + t;
+                const uint32_t c = (idx < p.m) ? (uint32_t)__ldg(p.x + idx) : 0u;
+                wv |= c << (L::BITS * t);
+            }
+            xw[q] = wv;
+        }
+    }
+    // Padding masks for the last PADU units of the thread.
+    uint32_t padm[PADU > 0 ? PADU : 1];
+#pragma unroll
+    for (int t = 0; t < PADU; ++t)
+        padm[t] = ((RP - PADU + t) >= nreal) ? L::MSB : 0u;
+
+    for (int e = lane; e < p.ring * NGRP; e += 32) ring[e] = 0u;
+    __syncwarp();
+
+    uint32_t h[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) h[k] = 0u;
+
+    // Columns (LCS) or pairs (score) combed by this tile.
+    const int64_t ncomb = (c1 - c0) + wk - 1;
+    const int64_t nunits = SCORE ? ncomb : (ncomb + 1) / 2;
+    const int64_t steps = nunits + G - 1;
+    const uint32_t wvec = (uint32_t)(SCORE ? 2 * wk : wk) * L::ONES;
+    const uint32_t inval_bias = (uint32_t)((1u << (L::BITS - 1)) - (uint32_t)wk) * L::ONES;
+    const int kdrop = SCORE ? p.renorm : 2 * p.renorm;
+    const uint32_t rr_bias = (uint32_t)((1u << (L::BITS - 1)) - (uint32_t)kdrop) * L::ONES;
+    const int ring_mask = p.ring - 1;
+    const int64_t ylast = p.n - 1;
+    const int64_t plot_cols = c1 - c0;
+
+    int kc = wk;        // key of the first seaweed starting in this thread's unit
+    int since = 0;      // steps since the last renormalisation
+    uint32_t d = 0;     // per strip: seaweeds counted in the current window
+    uint32_t vdown0 = 0, vdown1 = 0;
+
+    // Count one exit (Theorem 3.1's queue B, as a ring of flags by start).
+    // `col` is the combed column (LCS) or pair (score) index within the tile.
+    auto count_exit = [&](uint32_t ex, uint32_t knew, int64_t col) {
+        const uint32_t age = knew - ex;                       // per lane, >= 0
+        const uint32_t inval = (age + inval_bias) & L::MSB;   // age >= w
+        const uint32_t valid = (inval ^ L::MSB) >> (L::BITS - 1);
+        d += valid;
+#pragma unroll
+        for (int b = 0; b < NS; ++b) {
+            if ((valid >> (L::BITS * b)) & 1u) {
+                const int a = (int)((age >> (L::BITS * b)) & L::MASK);
+                uint32_t *e = ring + (int)((col - a) & ring_mask) * NGRP + grp;
+                *e += 1u << (L::BITS * b);
+            }
+        }
+    };
+    auto expire = [&](int64_t col) {        // start `col - w` leaves the window
+        if (col >= wk) {
+            uint32_t *e = ring + (int)((col - wk) & ring_mask) * NGRP + grp;
+            d -= *e;
+            *e = 0u;
+        }
+    };
+    auto stage_out = [&](int64_t col) {
+        if (col >= wk - 1 && col < ncomb)
+            stage[(int)((col - (wk - 1)) % kOB) * (NGRP + 1) + grp] = wvec - d;
+    };
+    auto maybe_flush = [&](int64_t col) {   // uniform across the warp
+        if (col >= wk - 1 && col < ncomb) {
+            const int64_t jo = col - (wk - 1);
+            if ((jo % kOB) == kOB - 1 || jo == plot_cols - 1) {
+                __syncwarp();
+                const int cnt = (int)(jo % kOB) + 1;
+                flush_stage<L, NGRP>(p, stage, iw, c0 + jo - (cnt - 1), cnt, lane);
+                __syncwarp();
+            }
+        }
+    };
+    auto ychar = [&](int64_t yi) -> uint32_t {
+        return (uint32_t)__ldg(p.y + (yi < 0 ? 0 : (yi > ylast ? ylast : yi)));
+    };
+
+    for (int64_t s = 0; s < steps; ++s) {
+        const int64_t u = s - g;          // this thread's unit
+        if (u > 0) {
+            kc += SCORE ? 1 : 2;
+            if (++since == p.renorm) {     // Proposition 3.4: old keys collapse to 0
+#pragma unroll
+                for (int k = 0; k < R; ++k) h[k] = renorm_key<L>(h[k], rr_bias);
+                kc = wk;
+                since = 0;
+            }
+        }
+        const uint32_t knew0 = (uint32_t)kc * L::ONES;
+        const uint32_t knew1 = SCORE ? knew0 : knew0 + L::ONES;
+
+        uint32_t va, vb;                  // top seaweeds of the two columns
+        if (G > 1) {
+            const uint32_t in0 = __shfl_up_sync(0xffffffffu, vdown0, 1);
+            const uint32_t in1 = __shfl_up_sync(0xffffffffu, vdown1, 1);
+            va = (g == 0) ? knew0 : in0;
+            vb = (g == 0) ? knew1 : in1;
+        } else {
+            va = knew0;
+            vb = knew1;
+        }
+
+        if (!SCORE) {
+            const uint32_t yb0 = ychar(c0 + 2 * u) * L::ONES;
+            const uint32_t yb1 = ychar(c0 + 2 * u + 1) * L::ONES;
+            uint32_t nz0[NQ], nz1[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                nz0[q] = mismatch_word<L>(xw[q], yb0);
+                nz1[q] = mismatch_word<L>(xw[q], yb1);
+            }
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const int q = k / L::RPW, r = k % L::RPW;
+                const uint32_t m0 = (r == 0) ? nz0[q] : row_shift<L>(nz0[q], nz0[q + 1], r);
+                const uint32_t m1 = (r == 0) ? nz1[q] : row_shift<L>(nz1[q], nz1[q + 1], r);
+                const int pi = k - (R - PADU);
+                const uint32_t pad = (pi >= 0) ? padm[pi < 0 ? 0 : pi] : 0u;
+                cell<L>(h[k], va, m0, pad);
+                cell<L>(h[k], vb, m1, pad);
+            }
+        } else {
+            const uint32_t yb = ychar(c0 + u) * L::ONES;
+            uint32_t nz[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) nz[q] = mismatch_word<L>(xw[q], yb);
+#pragma unroll
+            for (int q = 0; q < RP; ++q) {
+                const int pi = q - (RP - PADU);
+                const uint32_t pad = (pi >= 0) ? padm[pi < 0 ? 0 : pi] : 0u;
+                // '$' column: '$' row matches (unless padding), x row mismatches.
+                if (pi >= 0) {
+                    cell<L>(h[2 * q], va, pad, pad);
+                } else {
+                    const uint32_t tmp = h[2 * q];
+                    h[2 * q] = va;
+                    va = tmp;
+                }
+                cell_mismatch<L>(h[2 * q + 1], va);
+                // character column: '$' row mismatches, x row compares.
+                cell_mismatch<L>(h[2 * q], vb);
+                const int qq = q / L::RPW, r = q % L::RPW;
+                const uint32_t mm = (r == 0) ? nz[qq] : row_shift<L>(nz[qq], nz[qq + 1], r);
+                cell<L>(h[2 * q + 1], vb, mm, pad);
+            }
+        }
+        vdown0 = va;
+        vdown1 = vb;
+
+        // ---- bottom threads: count exits (Theorem 3.1) and stage the plot ----
+        const int64_t ubot = s - (G - 1);   // the bottom threads' unit (warp-uniform)
+        const bool bottom = (g == G - 1) && u >= 0 && u < nunits;
+        if (!SCORE) {
+            const int64_t col0 = 2 * ubot, col1 = 2 * ubot + 1;
+            if (bottom) {
+                expire(col0);
+                count_exit(va, knew0, col0);
+                stage_out(col0);
+            }
+            if (ubot >= 0) maybe_flush(col0);
+            if (bottom && col1 < ncomb) {
+                expire(col1);
+                count_exit(vb, knew1, col1);
+                stage_out(col1);
+            }
+            if (ubot >= 0) maybe_flush(col1);
+        } else {
+            if (bottom) {
+                expire(ubot);
+                count_exit(va, knew0, ubot);
+                count_exit(vb, knew0, ubot);
+                stage_out(ubot);
+            }
+            if (ubot >= 0) maybe_flush(ubot);
+        }
+    }
+}
+
+}  // namespace ap

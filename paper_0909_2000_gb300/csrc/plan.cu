@@ -1,0 +1,177 @@
+// plan.cu -- variant choice, tiling and the comb launch.
+#include <algorithm>
+#include <cstdio>
+#include <mutex>
+
+#include "plan.h"
+
+namespace ap {
+
+namespace {
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+const Variant *find_variant(int bits, int rows, int groups, bool score)
+{
+    int count = 0;
+    const Variant *t = variant_table(&count);
+    for (int i = 0; i < count; ++i)
+        if (t[i].lane_bits == bits && t[i].rows == rows && t[i].groups == groups &&
+            t[i].score == score)
+            return &t[i];
+    return nullptr;
+}
+
+int next_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+bool choose_variant(int w, bool score, Plan *pl, std::string *why)
+{
+    int bits = 0, rows = 0, groups = 0;
+    if (!score) {
+        if (w <= 120) {                       // 7-bit keys: w + renorm span <= 127
+            bits = 8; groups = 1; rows = (int)round_up(w, 8);
+        } else {
+            bits = 16;
+            for (int g : {2, 4, 8}) {
+                int r = (int)std::max<int64_t>(16, round_up(ceil_div(w, g), 8));
+                if (r <= 64) { groups = g; rows = r; break; }
+            }
+        }
+    } else {
+        if (w <= 64) {
+            bits = 8; groups = 1; rows = 2 * (int)round_up(w, 4);
+        } else if (w <= 120) {
+            bits = 8; groups = 2; rows = 2 * (int)round_up(ceil_div(w, 2), 4);
+        } else {
+            bits = 16; groups = 8;
+            int rp = (int)std::max<int64_t>(16, round_up(ceil_div(w, 8), 4));
+            if (rp <= 32) rows = 2 * rp;
+        }
+    }
+    const Variant *v = (rows > 0) ? find_variant(bits, rows, groups, score) : nullptr;
+    if (!v) {
+        if (why) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "no compiled comb variant for w=%d (%s mode)", w,
+                     score ? "score" : "LCS");
+            *why = buf;
+        }
+        return false;
+    }
+    pl->v = v;
+    pl->w = w;
+    pl->score = score;
+    pl->comb_rows = score ? 2 * w : w;
+    pl->max_value = score ? 2 * w : w;
+    const int half = 1 << (bits - 1);
+    pl->renorm = score ? (half - w) : (half - w) / 2;
+    pl->ring = next_pow2(w + 1);
+    pl->strips_per_warp = (32 / groups) * (bits == 8 ? 4 : 2);
+    const int ngrp = 32 / groups;
+    pl->smem = (size_t)kWarpsPerBlock * (size_t)(pl->ring * ngrp + kOB * (ngrp + 1)) * 4u;
+    return true;
+}
+
+void tile_plan(Plan *pl, int64_t rows, int64_t cols, int64_t chunk_hint, int device)
+{
+    pl->rows = rows;
+    pl->cols = cols;
+    pl->nsg = ceil_div(rows, pl->strips_per_warp);
+    int sms = 152;
+    if (device >= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && v > 0)
+            sms = v;
+        else
+            cudaGetLastError();
+    }
+    int64_t chunk;
+    if (chunk_hint > 0) {
+        chunk = round_up(chunk_hint, kOB);
+    } else {
+        // Enough tiles for several waves of ~8 resident warps per SM, but
+        // chunks long enough that the w - 1 warm-up columns stay small.
+        const int64_t want_tiles = (int64_t)sms * 8 * 4;
+        const int64_t nch = std::max<int64_t>(1, ceil_div(want_tiles, pl->nsg));
+        chunk = round_up(ceil_div(cols, nch), kOB);
+        chunk = std::max<int64_t>(chunk, round_up(16 * (int64_t)pl->w, kOB));
+    }
+    chunk = std::min<int64_t>(chunk, round_up(std::max<int64_t>(cols, 1), kOB));
+    pl->chunk = std::max<int64_t>(chunk, kOB);
+    pl->nchunks = ceil_div(cols, pl->chunk);
+    pl->ntiles = pl->nsg * pl->nchunks;
+}
+
+int64_t physical_cells(const Plan &pl)
+{
+    // every tile combs (its plot columns + w - 1) units of R rows x strips per warp
+    const int64_t units = pl.cols + pl.nchunks * (int64_t)(pl.w - 1);
+    const int64_t cols_phys = pl.score ? 2 * units : units;
+    const int64_t comb_rows_padded = (int64_t)pl.v->rows * pl.v->groups;
+    return pl.nsg * (int64_t)pl.strips_per_warp * cols_phys * comb_rows_padded;
+}
+
+cudaError_t launch_comb(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y,
+                        int64_t n, void *out, int out_bytes, int64_t ld, cudaStream_t stream)
+{
+    if (pl.ntiles == 0) return cudaSuccess;
+    static std::mutex mu;
+    {
+        // Raise the dynamic shared-memory limit of this kernel once per device.
+        static bool done[64][16] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        int count = 0;
+        const Variant *t = variant_table(&count);
+        const int vi = (int)(pl.v - t);
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 16 && vi < 64 && !done[vi][dev]) {
+            cudaError_t e = cudaFuncSetAttribute((const void *)pl.v->fn,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 96 * 1024);
+            if (e != cudaSuccess) return e;
+            done[vi][dev] = true;
+        }
+    }
+    CombParams p;
+    p.x = x;
+    p.y = y;
+    p.m = m;
+    p.n = n;
+    p.w = pl.w;
+    p.renorm = pl.renorm;
+    p.rows = pl.rows;
+    p.cols = pl.cols;
+    p.chunk = pl.chunk;
+    p.nsg = pl.nsg;
+    p.ntiles = pl.ntiles;
+    p.tile0 = 0;
+    p.out = out;
+    p.ld = ld;
+    p.out_bytes = out_bytes;
+    const uintptr_t a = (uintptr_t)out;
+    p.vec_ok = (out_bytes == 1) ? ((a % 4 == 0) && (ld % 4 == 0))
+                                : ((a % 8 == 0) && (ld % 4 == 0));
+    p.ring = pl.ring;
+    const int64_t blocks = ceil_div(pl.ntiles, kWarpsPerBlock);
+    // grid.x is limited to 2^31 - 1 blocks; split very large launches.
+    const int64_t max_blocks = 1LL << 30;
+    for (int64_t b0 = 0; b0 < blocks; b0 += max_blocks) {
+        const int64_t nb = std::min(max_blocks, blocks - b0);
+        p.tile0 = b0 * kWarpsPerBlock;
+        pl.v->fn<<<(unsigned)nb, kWarpsPerBlock * 32, pl.smem, stream>>>(p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace ap

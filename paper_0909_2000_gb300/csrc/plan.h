@@ -1,0 +1,40 @@
+// plan.h -- choosing a kernel variant and tiling for one plot.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include "variants.h"
+
+namespace ap {
+
+struct Plan {
+    const Variant *v = nullptr;
+    int w = 0;            // window length (key window)
+    bool score = false;   // '$'-interleaved ({2,1,0}) mode
+    int comb_rows = 0;    // physical comb height: w or 2w
+    int renorm = 0;       // steps between key renormalisations
+    int ring = 0;         // exit-ring slots (power of two > w)
+    int strips_per_warp = 0;
+    int64_t rows = 0, cols = 0;
+    int64_t chunk = 0, nchunks = 0, nsg = 0, ntiles = 0;
+    size_t smem = 0;      // dynamic shared memory per block
+    int max_value = 0;    // largest plot value: w or 2w
+};
+
+// Picks the variant for (w, score).  Returns false (with a message) when no
+// compiled variant covers it.
+bool choose_variant(int w, bool score, Plan *pl, std::string *why);
+
+// Tiles a rows x cols plot for the chosen variant.  `chunk_hint` > 0 forces
+// the column chunk (rounded up to a multiple of 32).
+void tile_plan(Plan *pl, int64_t rows, int64_t cols, int64_t chunk_hint, int device);
+
+// Launch one comb over `pl` on `stream`.
+cudaError_t launch_comb(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y,
+                        int64_t n, void *out, int out_bytes, int64_t ld, cudaStream_t stream);
+
+// Physical comb cell updates for a plan (warm-up and padding included).
+int64_t physical_cells(const Plan &pl);
+
+}  // namespace ap

@@ -1,0 +1,28 @@
+// variants.h -- registry of compiled strip-comb kernel variants.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "comb.cuh"
+
+namespace ap {
+
+typedef void (*comb_fn_t)(CombParams);
+
+struct Variant {
+    int lane_bits;   // 8 or 16
+    int rows;        // R: physical comb rows per thread
+    int groups;      // G: threads per strip group
+    bool score;      // '$'-interleaved strings
+    comb_fn_t fn;
+};
+
+// Filled by the instantiation units (variants_*.cu).
+const Variant *variant_table(int *count);
+
+}  // namespace ap
+
+// Instantiation helper: one template instance plus its registry entry.
+#define AP_VARIANT(LANES, BITS, R, G, SCORE, PADR)                                  \
+    { BITS, R, G, SCORE, &ap::comb_kernel<ap::LANES, R, G, SCORE, PADR> }

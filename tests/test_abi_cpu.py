@@ -1,0 +1,79 @@
+"""The C-ABI library builds, loads and exports every declared symbol (CPU only;
+no kernel is launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_0909_2000_gb300 as ap
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = ""
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            text += open(os.path.join(inc, f)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ap_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ["ap_alignment_plot", "ap_alignment_dots", "ap_plot_shape", "ap_plot_plan",
+              "ap_dots_workspace_size", "ap_plot_checksum", "ap_last_error"]:
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ap.load()
+    raw = ctypes.CDLL(ap.library_path())
+    missing = [s for s in declared_symbols() if not hasattr(raw, s)]
+    assert missing == []
+    assert "sm_103a" in ap.version()
+    assert lib is ap.load()
+
+
+def test_host_side_validation_without_gpu():
+    assert ap.plot_shape(512, 512, 16) == (496, 496)
+    assert ap.plot_shape(5, 9, 5) == (0, 4)
+    with pytest.raises(ap.ApError) as e:
+        ap.plot_shape(10, 10, 0)
+    assert e.value.status == ap.AP_E_INVAL
+    with pytest.raises(ap.ApError) as e:
+        ap.plot_plan(100, 100, 10, (3, 1, 0))
+    assert e.value.status == ap.AP_E_UNSUPPORTED
+    with pytest.raises(ap.ApError) as e:
+        ap.plot_plan(100, 100, 10, (1, 1, 0))     # not normalised
+    assert e.value.status == ap.AP_E_INVAL
+    with pytest.raises(ap.ApError) as e:
+        ap.plot_plan(100, 100, 10, (1, 0, -1))
+    assert e.value.status == ap.AP_E_INVAL
+    with pytest.raises(ap.ApError) as e:
+        ap.plot_plan(100000, 100000, 600)
+    assert e.value.status == ap.AP_E_UNSUPPORTED
+    with pytest.raises(ap.ApError):
+        ap.set_chunk(-1)
+
+
+@pytest.mark.parametrize("w,scores", [(1, ap.LCS), (16, ap.LCS), (100, ap.LCS), (120, ap.LCS),
+                                      (121, ap.LCS), (256, ap.LCS), (512, ap.LCS), (1, ap.SCORE),
+                                      (64, ap.SCORE), (65, ap.SCORE), (120, ap.SCORE),
+                                      (121, ap.SCORE), (256, ap.SCORE)])
+def test_every_supported_window_has_a_variant(w, scores):
+    pl = ap.plot_plan(w + 1000, w + 777, w, scores)
+    rows = 2 * w if scores == ap.SCORE else w
+    assert pl["comb_rows"] == rows
+    assert pl["rows_per_lane"] * pl["lanes_per_strip"] >= rows
+    assert pl["logical_cells"] == 1000 * 777 * w
+    assert pl["physical_cells"] >= pl["logical_cells"] * (4 if scores == ap.SCORE else 1)
+
+
+def test_plan_of_the_100k_plot():
+    pl = ap.plot_plan(100_000, 100_000, 100)
+    assert pl["lane_bits"] == 8 and pl["strips_per_reg"] == 4 and pl["lanes_per_strip"] == 1
+    # warm-up and padding overhead stay small
+    assert pl["physical_cells"] < 1.06 * pl["logical_cells"]

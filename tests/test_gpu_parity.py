@@ -1,0 +1,181 @@
+"""CUDA path against the oracle, element by element (needs a GPU).
+
+Every call goes through the C ABI (libalnplot.so) via the ctypes binding."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0909_2000_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint8)).cuda()
+
+
+def gpu_plot(ap, x, y, w, scores=(1, 0, 0), out_dtype=None):
+    p = ap.alignment_plot(dev(x), dev(y), w, scores, out_dtype=out_dtype)
+    torch.cuda.synchronize()
+    return p.cpu().numpy().astype(np.int64)
+
+
+def test_plot_512_matches_oracle_and_golden(cuda_lib):
+    ap = cuda_lib
+    c = synth.dna_plot_512(0)
+    g = gpu_plot(ap, c.x, c.y, c.w)
+    o = oracle.plot(c.x, c.y, c.w)
+    assert g.shape == (496, 496)
+    assert np.array_equal(g, o)
+
+
+CASES = [
+    # (m, n, w, alphabet, scores)
+    (40, 37, 1, b"AC", (1, 0, 0)),
+    (70, 333, 5, b"ACGT", (1, 0, 0)),
+    (300, 301, 16, b"ACGT", (1, 0, 0)),
+    (257, 1000, 31, b"AB", (1, 0, 0)),
+    (700, 650, 100, b"ACGT", (1, 0, 0)),
+    (300, 999, 117, b"ACGT", (1, 0, 0)),
+    (400, 420, 120, b"ACGTN", (1, 0, 0)),
+    (200, 900, 121, b"ACGT", (1, 0, 0)),
+    (300, 500, 128, b"ACGT", (1, 0, 0)),
+    (400, 700, 200, b"AC", (1, 0, 0)),
+    (600, 600, 256, b"ACGT", (1, 0, 0)),
+    (40, 45, 3, b"AC", (2, 1, 0)),
+    (190, 211, 16, b"ACDEFGHIKLMNPQRSTVWY", (2, 1, 0)),
+    (300, 333, 64, b"ACDEFGHIKLMNPQRSTVWY", (2, 1, 0)),
+    (250, 270, 63, b"ACGT", (2, 1, 0)),
+    (300, 310, 65, b"ACGT", (2, 1, 0)),
+    (300, 330, 99, b"ACGT", (2, 1, 0)),
+    (400, 401, 120, b"ACGT", (2, 1, 0)),
+    (420, 430, 121, b"ACGT", (2, 1, 0)),
+    (600, 640, 200, b"AC", (2, 1, 0)),
+]
+
+
+@pytest.mark.parametrize("m,n,w,alph,scores", CASES)
+def test_random_shapes(cuda_lib, m, n, w, alph, scores):
+    ap = cuda_lib
+    seed = m * 7 + n * 3 + w
+    x = synth.alphabet_string(seed, 1, m, np.frombuffer(alph, np.uint8))
+    y = synth.alphabet_string(seed, 2, n, np.frombuffer(alph, np.uint8))
+    vmax = 2 * w if scores[0] == 2 else w
+    g = gpu_plot(ap, x, y, w, scores, torch.uint8 if vmax <= 255 else torch.int16)
+    o = oracle.plot(x, y, w, scores[0], scores[1])
+    assert g.shape == o.shape
+    bad = np.argwhere(g != o)
+    assert len(bad) == 0, "first mismatches %s: gpu %s oracle %s" % (
+        bad[:4].tolist(), g[tuple(bad[:4].T)].tolist(), o[tuple(bad[:4].T)].tolist())
+
+
+@pytest.mark.parametrize("w,scores", [(9, (1, 0, 0)), (100, (1, 0, 0)), (150, (1, 0, 0)),
+                                      (20, (2, 1, 0)), (90, (2, 1, 0))])
+def test_tiny_chunks_cross_many_tiles(cuda_lib, w, scores):
+    ap = cuda_lib
+    x = synth.dna(5, 1, w + 140)
+    y = synth.dna(5, 2, w + 1000)
+    o = oracle.plot(x, y, w, scores[0], scores[1])
+    try:
+        ap.set_chunk(32)
+        g = gpu_plot(ap, x, y, w, scores, torch.int16)
+    finally:
+        ap.set_chunk(0)
+    assert np.array_equal(g, o)
+
+
+def test_all_byte_values_and_identical_windows(cuda_lib):
+    ap = cuda_lib
+    x = np.concatenate([np.arange(256), np.arange(256)[::-1], np.arange(0, 256, 3)]).astype(np.uint8)
+    y = np.concatenate([np.arange(256)[::-1], np.arange(256), synth.dna(1, 1, 100)]).astype(np.uint8)
+    for w in (8, 33, 130):
+        for sc in ((1, 0, 0), (2, 1, 0)):
+            o = oracle.plot(x, y, w, sc[0], sc[1])
+            g = gpu_plot(ap, x, y, w, sc, torch.int16)
+            assert np.array_equal(g, o), (w, sc)
+
+
+def test_empty_and_degenerate(cuda_lib):
+    ap = cuda_lib
+    x = dev(synth.dna(2, 1, 10))
+    y = dev(synth.dna(2, 2, 30))
+    assert ap.alignment_plot(x, y, 10).shape == (0, 20)
+    assert ap.alignment_plot(y, x, 12).shape == (18, 0)
+    assert ap.alignment_plot(x, x, 11).shape == (0, 0)
+    p = ap.alignment_plot(y, y, 1)          # w = 1: exact character equality
+    torch.cuda.synchronize()
+    ya = synth.dna(2, 2, 30)
+    assert np.array_equal(p.cpu().numpy(), (ya[:29, None] == ya[None, :29]).astype(np.uint8))
+
+
+def test_strided_and_wide_outputs(cuda_lib):
+    ap = cuda_lib
+    x, y = synth.dna(3, 1, 230), synth.dna(3, 2, 310)
+    o = oracle.plot(x, y, 30)
+    for ld, dt in [(280, torch.uint8), (283, torch.uint8), (301, torch.int16), (288, torch.int16)]:
+        buf = torch.full((200, ld), 255, dtype=dt, device="cuda")
+        view = buf[:, :280]
+        ap.alignment_plot(dev(x), dev(y), 30, out=view)
+        torch.cuda.synchronize()
+        b = buf.cpu().numpy().astype(np.int64)
+        assert np.array_equal(b[:, :280], o), ld
+        if ld > 280:
+            assert np.all(b[:, 280:] == (255 if dt == torch.uint8 else 255))
+
+
+def test_validation_errors(cuda_lib):
+    ap = cuda_lib
+    x, y = dev(synth.dna(4, 1, 300)), dev(synth.dna(4, 2, 300))
+    with pytest.raises(ap.ApError) as e:
+        ap.alignment_plot(x, y, 200, out_dtype=torch.uint8, scores=(2, 1, 0))   # 2w > 255
+    assert e.value.status == ap.AP_E_INVAL
+    small = torch.empty((100, 150), dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):
+        ap.alignment_plot(x, y, 100, out=small)
+
+
+def test_plot_checksum_kernel(cuda_lib):
+    ap = cuda_lib
+    c = synth.dna_plot_512(0)
+    p = ap.alignment_plot(dev(c.x), dev(c.y), c.w)
+    cs, hist = ap.plot_checksum(p, c.w + 1)
+    o = oracle.plot(c.x, c.y, c.w)
+    assert cs == oracle.checksum(o)
+    assert hist.tolist() == oracle.histogram(o, c.w + 1).tolist()
+
+
+@pytest.mark.parametrize("w,thr,scores", [(16, 11, (1, 0, 0)), (40, 29, (1, 0, 0)),
+                                          (24, 40, (2, 1, 0)), (130, 90, (1, 0, 0))])
+def test_dots_match_oracle(cuda_lib, w, thr, scores):
+    ap = cuda_lib
+    x = synth.dna(6, 1, 700)
+    y, _ = synth.plant(x, synth.dna(6, 2, 800), 2, 200, 6, 50, synth.DNA, 0.1, 0.05)
+    o = oracle.dots(oracle.plot(x, y, w, scores[0], scores[1]), thr)
+    dots, count = ap.alignment_dots(dev(x), dev(y), w, thr, scores)
+    torch.cuda.synchronize()
+    assert count == len(o)
+    assert np.array_equal(ap.dots_to_numpy(dots, count), o)
+    # from a materialised plot as well
+    p = ap.alignment_plot(dev(x), dev(y), w, scores, out_dtype=torch.int16)
+    d2, c2 = ap.plot_dots(p, thr)
+    assert c2 == len(o) and np.array_equal(ap.dots_to_numpy(d2, c2), o)
+
+
+def test_dots_overflow_reports_full_count(cuda_lib):
+    ap = cuda_lib
+    x, y = synth.dna(7, 1, 300), synth.dna(7, 2, 300)
+    o = oracle.dots(oracle.plot(x, y, 12), 8)
+    assert len(o) > 10
+    with pytest.raises(ap.ApError) as e:
+        ap.alignment_dots(dev(x), dev(y), 12, 8, cap=10)
+    assert e.value.status == ap.AP_E_OVERFLOW
+    dots = torch.empty((10, 3), dtype=torch.int32, device="cuda")
+    try:
+        ap.alignment_dots(dev(x), dev(y), 12, 8, dots=dots, cap=10)
+    except ap.ApError as err:
+        assert err.status == ap.AP_E_OVERFLOW
+    assert np.array_equal(ap.dots_to_numpy(dots, 10), o[:10])
