@@ -46,7 +46,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lcs_dna_100k_w100",
-                    choices=["lcs_dna_100k_w100", "lcs_dna_512_w16", "score_protein_20k_w64"])
+                    choices=["lcs_dna_100k_w100", "lcs_dna_512_w16", "score_protein_20k_w64",
+                             "lcs_dna_20k_w100"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -59,6 +60,8 @@ def workload(name):
         return synth.dna_plot_100k(0)
     if name == "lcs_dna_512_w16":
         return synth.dna_plot_512(0)
+    if name == "lcs_dna_20k_w100":
+        return synth.dna_plot_20k(0)
     return synth.protein_score_20k(0)
 
 

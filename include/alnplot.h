@@ -120,6 +120,15 @@ ap_status ap_plot_plan(int64_t m, int64_t n, int32_t w,
 ap_status ap_set_chunk(int64_t chunk);
 
 /*
+ * Tuning: ask for `groups` threads per group of strips (the comb rows of one
+ * strip are split over them; 0 restores the automatic choice).  Honoured
+ * when a compiled variant exists for the window length, else the automatic
+ * choice is used.  Results do not depend on it.  Process-wide; AP_E_INVAL
+ * unless groups is 0, 1, 2, 4 or 8.
+ */
+ap_status ap_set_lanes_per_strip(int32_t groups);
+
+/*
  * Full alignment plot (Section 2 definition; Theorem 3.1 / Section 3 method).
  *
  *   x       device, m bytes          y       device, n bytes

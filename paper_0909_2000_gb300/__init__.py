@@ -19,7 +19,7 @@ import threading
 
 __all__ = [
     "load", "ApError", "LCS", "SCORE", "plot_shape", "plot_plan", "alignment_plot",
-    "alignment_dots", "plot_dots", "plot_checksum", "version", "set_chunk", "DOT_DTYPE_FIELDS",
+    "alignment_dots", "plot_dots", "plot_checksum", "version", "set_chunk", "set_lanes_per_strip", "DOT_DTYPE_FIELDS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -65,6 +65,7 @@ def _declare(lib):
     lib.ap_status_string.argtypes = [ctypes.c_int]
     sigs = {
         "ap_set_chunk": [i64],
+        "ap_set_lanes_per_strip": [i32],
         "ap_plot_shape": [i64, i64, i32, i64p, i64p],
         "ap_plot_plan": [i64, i64, i32, sc, ctypes.POINTER(ap_plan)],
         "ap_alignment_plot": [p, i64, p, i64, i32, sc, p, i32, i64, p],
@@ -136,6 +137,11 @@ def _dev_u8(t, name):
 def set_chunk(chunk: int) -> None:
     """Force plot columns per tile (0 = automatic); results do not change."""
     _check(load().ap_set_chunk(int(chunk)))
+
+
+def set_lanes_per_strip(groups: int) -> None:
+    """Force threads per strip group (0 = automatic); results do not change."""
+    _check(load().ap_set_lanes_per_strip(int(groups)))
 
 
 def plot_shape(m: int, n: int, w: int) -> tuple[int, int]:

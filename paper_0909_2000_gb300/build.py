@@ -28,6 +28,10 @@ def _variants():
     # LCS, 8-bit keys, one thread per strip group: w <= 120, R = roundup(w, 8)
     for r in range(8, 121, 8):
         v.append(("U8Lanes", 8, r, 1, False, 8))
+    # LCS, 8-bit keys, a strip group's rows split over 2 or 4 threads
+    for g, rs in ((2, range(16, 61, 4)), (4, range(8, 33, 4))):
+        for r in rs:
+            v.append(("U8Lanes", 8, r, g, False, 8))
     # score mode, 8-bit keys: w <= 64 on one thread, w <= 120 on two
     for rp in range(4, 65, 4):
         v.append(("U8Lanes", 8, 2 * rp, 1, True, 8))

@@ -13,6 +13,7 @@ namespace ap {
 
 static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_chunk_override{0};
+static std::atomic<int32_t> g_groups_override{0};
 
 ap_status fail(ap_status s, const char *fmt, ...)
 {
@@ -63,7 +64,8 @@ ap_status make_plan(int64_t m, int64_t n, int32_t w, const ap_scores *scores, Pl
     ap_status s = score_mode(scores, &score);
     if (s != AP_OK) return s;
     std::string why;
-    if (!choose_variant(w, score, pl, &why)) return fail(AP_E_UNSUPPORTED, "%s", why.c_str());
+    if (!choose_variant(w, score, g_groups_override.load(), pl, &why))
+        return fail(AP_E_UNSUPPORTED, "%s", why.c_str());
     const int64_t rows = std::max<int64_t>(0, m - w), cols = std::max<int64_t>(0, n - w);
     tile_plan(pl, rows, cols, g_chunk_override.load(), current_device());
     return AP_OK;
@@ -128,6 +130,14 @@ ap_status ap_set_chunk(int64_t chunk)
 {
     if (chunk < 0) return fail(AP_E_INVAL, "chunk = %lld: must be >= 0", (long long)chunk);
     g_chunk_override.store(chunk);
+    return AP_OK;
+}
+
+ap_status ap_set_lanes_per_strip(int32_t groups)
+{
+    if (groups != 0 && groups != 1 && groups != 2 && groups != 4 && groups != 8)
+        return fail(AP_E_INVAL, "lanes per strip = %d: must be 0 (automatic), 1, 2, 4 or 8", groups);
+    g_groups_override.store(groups);
     return AP_OK;
 }
 

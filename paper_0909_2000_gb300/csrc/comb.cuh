@@ -71,6 +71,12 @@ struct CombParams {
     int32_t out_bytes;  // 1 or 2
     int32_t vec_ok;     // output pointer/ld allow aligned vector stores
     int32_t ring;       // ring slots (power of two > w)
+    // Runtime constants for the FMA-pipe forms of shifts and adds: one = 1,
+    // shmul[r] = 2^(32 - 8r) for byte shifts r = 1..3.  Passed at run time so
+    // the compiler keeps them as integer multiply-adds (FMA pipe) instead of
+    // turning them into ALU shifts; the ALU pipe is the comb's bottleneck.
+    uint32_t one;
+    uint32_t shmul[4];
 };
 
 // ---------------------------------------------------------------------------
@@ -108,38 +114,66 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
     return r;
 }
 
-// Row register for rows r = 1..RPW-1 past an aligned word: the lanes start r
-// characters further into the x stream.
-template <class L>
-__device__ __forceinline__ uint32_t row_shift(uint32_t a, uint32_t b, int r)
+__device__ __forceinline__ uint32_t mul_hi(uint32_t a, uint32_t b)
 {
-    if (L::BITS == 8) return prmt(a, b, 0x3210u + 0x1111u * (uint32_t)r);
-    return prmt(a, b, 0x5432u);   // r == 1 for 16-bit lanes
+    uint32_t r;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+
+// Row register for rows r = 1..RPW-1 past an aligned word: the lanes start r
+// characters further into the x stream, i.e. the 64-bit pair (b:a) shifted
+// right by 8r bits = (a >> 8r) | (b << (32 - 8r)).  Both halves are integer
+// multiplies by s = 2^(32 - 8r) (high and low word), so the shift runs on the
+// FMA pipe and leaves the ALU pipe to the cells.
+__device__ __forceinline__ uint32_t row_shift(uint32_t a, uint32_t b, uint32_t s)
+{
+    return mad_lo(b, s, mul_hi(a, s));
 }
 
 // Mismatch flags of one aligned word: lane MSB set iff x != y (any byte
 // values).  ((e & LOW) + LOW) has its MSB set iff the low bits of e are
-// nonzero, and never carries across lanes.  OR-ing e adds the top bit.
+// nonzero, and never carries across lanes.  OR-ing e adds the top bit.  The
+// add is a multiply-add by one (FMA pipe).
 template <class L>
-__device__ __forceinline__ uint32_t mismatch_word(uint32_t xw, uint32_t yb)
+__device__ __forceinline__ uint32_t mismatch_word(uint32_t xw, uint32_t yb, uint32_t one)
 {
-    uint32_t e = xw ^ yb;
-    return ((e & L::LOW) + L::LOW) | e;
+    return mad_lo((xw ^ yb) & L::LOW, one, L::LOW) | (xw ^ yb);
+}
+
+// Full-lane mismatch mask of one aligned word: 0xFF.. in lanes where x != y.
+template <class L>
+__device__ __forceinline__ uint32_t mismatch_mask(uint32_t xw, uint32_t yb, uint32_t one)
+{
+    return prmt(mismatch_word<L>(xw, yb, one), 0u, L::SIGNREP);
 }
 
 // One comb cell on NS strips at once.
 //   h: seaweed entering from the left (stays in the row register),
 //   v: seaweed entering from the top (travels down the column),
-//   nz: lane MSB set iff mismatch, pad: lane MSB set iff the row is padding
-//   (a padding row never matches).
+//   mm: full-lane mask, all ones where the cell is a mismatch (a padding row
+//   is all ones: it never matches).
 // Bottom output = h where (match or h >= v), else v; right output = other.
+// The match is folded into the left key, hc = h | 0x80 in mismatch lanes and
+// 0xFF in match lanes, so one subtraction hc - v (a multiply-add on the FMA
+// pipe) gives the swap decision in each lane's top bit: always in a match
+// lane, and h >= v otherwise (keys are at most 0x7F.., no borrow between
+// lanes).  hc does not depend on v, so the dependency chain from one cell to
+// the next is three instructions: subtract, sign-spread, select.
 template <class L>
-__device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t nz, uint32_t pad)
+__device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t mm, uint32_t neg1)
 {
-    uint32_t t = h - v + L::MSB;             // lane MSB: h >= v (no cross-lane carry)
-    uint32_t ms = t | (~nz & ~pad);          // lane MSB: swap
-    uint32_t M = prmt(ms, 0u, L::SIGNREP);   // full-lane swap mask
-    uint32_t vn = (h & M) | (v & ~M);
+    const uint32_t hc = h | ~mm | L::MSB;
+    const uint32_t t = mad_lo(v, neg1, hc);   // hc - v
+    const uint32_t M = prmt(t, 0u, L::SIGNREP);
+    const uint32_t vn = (h & M) | (v & ~M);
     h = h ^ v ^ vn;
     v = vn;
 }
@@ -157,9 +191,9 @@ __device__ __forceinline__ void cell_mismatch(uint32_t &h, uint32_t &v)
 
 // Keys drop by rr, saturating at 0.
 template <class L>
-__device__ __forceinline__ uint32_t renorm_key(uint32_t k, uint32_t rr_bias)
+__device__ __forceinline__ uint32_t renorm_key(uint32_t k, uint32_t rr_bias, uint32_t one)
 {
-    uint32_t t = k + rr_bias;                 // lane: k + (half - rr), MSB iff k >= rr
+    uint32_t t = mad_lo(k, one, rr_bias);     // lane: k + (half - rr), MSB iff k >= rr
     uint32_t M = prmt(t, 0u, L::SIGNREP);
     return t & M & L::LOW;
 }
@@ -312,11 +346,12 @@ comb_kernel(CombParams p)
             xw[q] = wv;
         }
     }
-    // Padding masks for the last PADU units of the thread.
+    // Padding masks for the last PADU units of the thread (all ones: the
+    // row never matches).
     uint32_t padm[PADU > 0 ? PADU : 1];
 #pragma unroll
     for (int t = 0; t < PADU; ++t)
-        padm[t] = ((RP - PADU + t) >= nreal) ? L::MSB : 0u;
+        padm[t] = ((RP - PADU + t) >= nreal) ? 0xFFFFFFFFu : 0u;
 
     for (int e = lane; e < p.ring * NGRP; e += 32) ring[e] = 0u;
     __syncwarp();
@@ -325,72 +360,110 @@ comb_kernel(CombParams p)
 #pragma unroll
     for (int k = 0; k < R; ++k) h[k] = 0u;
 
-    // Columns (LCS) or pairs (score) combed by this tile.
-    const int64_t ncomb = (c1 - c0) + wk - 1;
-    const int64_t nunits = SCORE ? ncomb : (ncomb + 1) / 2;
-    const int64_t steps = nunits + G - 1;
+    // Columns (LCS) or pairs (score) combed by this tile (chunks are capped at
+    // 2^30 columns, so tile-local indices fit in 32 bits).
+    const int ncomb = (int)(c1 - c0) + wk - 1;
+    const int nunits = SCORE ? ncomb : (ncomb + 1) / 2;
+    const int steps = nunits + G - 1;
     const uint32_t wvec = (uint32_t)(SCORE ? 2 * wk : wk) * L::ONES;
     const uint32_t inval_bias = (uint32_t)((1u << (L::BITS - 1)) - (uint32_t)wk) * L::ONES;
     const int kdrop = SCORE ? p.renorm : 2 * p.renorm;
     const uint32_t rr_bias = (uint32_t)((1u << (L::BITS - 1)) - (uint32_t)kdrop) * L::ONES;
     const int ring_mask = p.ring - 1;
-    const int64_t ylast = p.n - 1;
-    const int64_t plot_cols = c1 - c0;
+    const uint32_t ring_maskv = (uint32_t)ring_mask * L::ONES;
+    const int plot_cols = (int)(c1 - c0);
+    const uint8_t *ytile = p.y + c0;                  // y of this tile
+    const int ylast = (int)(p.n - 1 - c0);            // last valid index into ytile
+
+    const uint32_t one = p.one;
+    const uint32_t neg1 = 0u - p.one;
+    const uint32_t sh1 = p.shmul[1], sh2 = p.shmul[2], sh3 = p.shmul[3];
+    // multiplier of the byte shift for rows r = 1..RPW-1 past an aligned word
+    auto shm = [&](int r) -> uint32_t {
+        return (L::BITS == 16) ? sh2 : (r == 1 ? sh1 : (r == 2 ? sh2 : sh3));
+    };
 
     int kc = wk;        // key of the first seaweed starting in this thread's unit
     int since = 0;      // steps since the last renormalisation
     uint32_t d = 0;     // per strip: seaweeds counted in the current window
     uint32_t vdown0 = 0, vdown1 = 0;
 
-    // Count one exit (Theorem 3.1's queue B, as a ring of flags by start).
-    // `col` is the combed column (LCS) or pair (score) index within the tile.
-    auto count_exit = [&](uint32_t ex, uint32_t knew, int64_t col) {
+    // Exit counting (Theorem 3.1's queue B as a ring of "left validly" flags,
+    // one byte per strip, indexed by start column (LCS) or pair (score)).
+    //
+    // 8-bit keys: keys never exceed ring - 1 (the plan derives the key range
+    // from the ring size), so every age is below the ring size.  An exit too
+    // old for the window (age >= w) then maps to the slot of a start older
+    // than the window, which is already zero and is next read only after a
+    // later start re-uses it.  Storing its zero flag there is harmless, so
+    // the update needs no branch: each strip stores its 0/1 flag.  The four
+    // slots come from one byte-wise subtraction.
+    uint8_t *ring8 = (uint8_t *)(ring + grp);
+    auto count_exit = [&](uint32_t ex, uint32_t knew, int col) {
         const uint32_t age = knew - ex;                       // per lane, >= 0
         const uint32_t inval = (age + inval_bias) & L::MSB;   // age >= w
         const uint32_t valid = (inval ^ L::MSB) >> (L::BITS - 1);
         d += valid;
+        if (L::BITS == 8) {
+            const uint32_t colb = (uint32_t)(col & ring_mask) * L::ONES;
+            const uint32_t slots = (colb + L::MSB - age) & ring_maskv;   // (col - age) mod ring
 #pragma unroll
-        for (int b = 0; b < NS; ++b) {
-            if ((valid >> (L::BITS * b)) & 1u) {
-                const int a = (int)((age >> (L::BITS * b)) & L::MASK);
-                uint32_t *e = ring + (int)((col - a) & ring_mask) * NGRP + grp;
-                *e += 1u << (L::BITS * b);
+            for (int b = 0; b < NS; ++b) {
+                const uint32_t slot = (slots >> (8 * b)) & (uint32_t)ring_mask;
+                uint8_t *e = ring8 + slot * (uint32_t)(NGRP * 4) + b;
+                const uint8_t f = (uint8_t)((valid >> (8 * b)) & 1u);
+                if (SCORE) *e = (uint8_t)(*e + f);
+                else *e = f;
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                if ((valid >> (L::BITS * b)) & 1u) {
+                    const int a = (int)((age >> (L::BITS * b)) & L::MASK);
+                    uint32_t *e = ring + ((col - a) & ring_mask) * NGRP + grp;
+                    *e += 1u << (L::BITS * b);
+                }
             }
         }
     };
-    auto expire = [&](int64_t col) {        // start `col - w` leaves the window
-        if (col >= wk) {
-            uint32_t *e = ring + (int)((col - wk) & ring_mask) * NGRP + grp;
+    auto expire = [&](int col) {            // start `col - w` leaves the window
+        // (8-bit keys: for col < w the slot belongs to a future start and is 0)
+        if (L::BITS == 8 || col >= wk) {
+            uint32_t *e = ring + ((col - wk) & ring_mask) * NGRP + grp;
             d -= *e;
             *e = 0u;
         }
     };
-    auto stage_out = [&](int64_t col) {
+    auto stage_out = [&](int col) {
         if (col >= wk - 1 && col < ncomb)
-            stage[(int)((col - (wk - 1)) % kOB) * (NGRP + 1) + grp] = wvec - d;
+            stage[((col - (wk - 1)) % kOB) * (NGRP + 1) + grp] = wvec - d;
     };
-    auto maybe_flush = [&](int64_t col) {   // uniform across the warp
+    auto maybe_flush = [&](int col) {       // uniform across the warp
         if (col >= wk - 1 && col < ncomb) {
-            const int64_t jo = col - (wk - 1);
+            const int jo = col - (wk - 1);
             if ((jo % kOB) == kOB - 1 || jo == plot_cols - 1) {
                 __syncwarp();
-                const int cnt = (int)(jo % kOB) + 1;
+                const int cnt = (jo % kOB) + 1;
                 flush_stage<L, NGRP>(p, stage, iw, c0 + jo - (cnt - 1), cnt, lane);
                 __syncwarp();
             }
         }
     };
-    auto ychar = [&](int64_t yi) -> uint32_t {
-        return (uint32_t)__ldg(p.y + (yi < 0 ? 0 : (yi > ylast ? ylast : yi)));
+    // One thread per strip group: every column it reads lies inside y (the
+    // last column a tile combs, plus the odd padding column of a two-column
+    // step, is at most n - 1).  Skewed threads clamp.
+    auto ychar = [&](int yi) -> uint32_t {
+        if (G > 1) yi = yi < 0 ? 0 : (yi > ylast ? ylast : yi);
+        return (uint32_t)__ldg(ytile + yi);
     };
 
-    for (int64_t s = 0; s < steps; ++s) {
-        const int64_t u = s - g;          // this thread's unit
+    for (int s = 0; s < steps; ++s) {
+        const int u = s - g;              // this thread's unit
         if (u > 0) {
             kc += SCORE ? 1 : 2;
             if (++since == p.renorm) {     // Proposition 3.4: old keys collapse to 0
 #pragma unroll
-                for (int k = 0; k < R; ++k) h[k] = renorm_key<L>(h[k], rr_bias);
+                for (int k = 0; k < R; ++k) h[k] = renorm_key<L>(h[k], rr_bias, one);
                 kc = wk;
                 since = 0;
             }
@@ -410,36 +483,39 @@ comb_kernel(CombParams p)
         }
 
         if (!SCORE) {
-            const uint32_t yb0 = ychar(c0 + 2 * u) * L::ONES;
-            const uint32_t yb1 = ychar(c0 + 2 * u + 1) * L::ONES;
-            uint32_t nz0[NQ], nz1[NQ];
+            const uint32_t yb0 = ychar(2 * u) * L::ONES;
+            const uint32_t yb1 = ychar(2 * u + 1) * L::ONES;
+            uint32_t mm0[NQ], mm1[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                nz0[q] = mismatch_word<L>(xw[q], yb0);
-                nz1[q] = mismatch_word<L>(xw[q], yb1);
+                mm0[q] = mismatch_mask<L>(xw[q], yb0, one);
+                mm1[q] = mismatch_mask<L>(xw[q], yb1, one);
             }
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 const int q = k / L::RPW, r = k % L::RPW;
-                const uint32_t m0 = (r == 0) ? nz0[q] : row_shift<L>(nz0[q], nz0[q + 1], r);
-                const uint32_t m1 = (r == 0) ? nz1[q] : row_shift<L>(nz1[q], nz1[q + 1], r);
+                uint32_t m0 = (r == 0) ? mm0[q] : row_shift(mm0[q], mm0[q + 1], shm(r));
+                uint32_t m1 = (r == 0) ? mm1[q] : row_shift(mm1[q], mm1[q + 1], shm(r));
                 const int pi = k - (R - PADU);
-                const uint32_t pad = (pi >= 0) ? padm[pi < 0 ? 0 : pi] : 0u;
-                cell<L>(h[k], va, m0, pad);
-                cell<L>(h[k], vb, m1, pad);
+                if (pi >= 0) {
+                    m0 |= padm[pi < 0 ? 0 : pi];
+                    m1 |= padm[pi < 0 ? 0 : pi];
+                }
+                cell<L>(h[k], va, m0, neg1);
+                cell<L>(h[k], vb, m1, neg1);
             }
         } else {
-            const uint32_t yb = ychar(c0 + u) * L::ONES;
-            uint32_t nz[NQ];
+            const uint32_t yb = ychar(u) * L::ONES;
+            uint32_t mm[NQ];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) nz[q] = mismatch_word<L>(xw[q], yb);
+            for (int q = 0; q < NQ; ++q) mm[q] = mismatch_mask<L>(xw[q], yb, one);
 #pragma unroll
             for (int q = 0; q < RP; ++q) {
                 const int pi = q - (RP - PADU);
                 const uint32_t pad = (pi >= 0) ? padm[pi < 0 ? 0 : pi] : 0u;
                 // '$' column: '$' row matches (unless padding), x row mismatches.
                 if (pi >= 0) {
-                    cell<L>(h[2 * q], va, pad, pad);
+                    cell<L>(h[2 * q], va, pad, neg1);
                 } else {
                     const uint32_t tmp = h[2 * q];
                     h[2 * q] = va;
@@ -449,18 +525,19 @@ comb_kernel(CombParams p)
                 // character column: '$' row mismatches, x row compares.
                 cell_mismatch<L>(h[2 * q], vb);
                 const int qq = q / L::RPW, r = q % L::RPW;
-                const uint32_t mm = (r == 0) ? nz[qq] : row_shift<L>(nz[qq], nz[qq + 1], r);
-                cell<L>(h[2 * q + 1], vb, mm, pad);
+                uint32_t mq = (r == 0) ? mm[qq] : row_shift(mm[qq], mm[qq + 1], shm(r));
+                if (pi >= 0) mq |= pad;
+                cell<L>(h[2 * q + 1], vb, mq, neg1);
             }
         }
         vdown0 = va;
         vdown1 = vb;
 
         // ---- bottom threads: count exits (Theorem 3.1) and stage the plot ----
-        const int64_t ubot = s - (G - 1);   // the bottom threads' unit (warp-uniform)
+        const int ubot = s - (G - 1);       // the bottom threads' unit (warp-uniform)
         const bool bottom = (g == G - 1) && u >= 0 && u < nunits;
         if (!SCORE) {
-            const int64_t col0 = 2 * ubot, col1 = 2 * ubot + 1;
+            const int col0 = 2 * ubot, col1 = 2 * ubot + 1;
             if (bottom) {
                 expire(col0);
                 count_exit(va, knew0, col0);

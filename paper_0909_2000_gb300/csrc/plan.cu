@@ -32,11 +32,15 @@ int next_pow2(int v)
 
 }  // namespace
 
-bool choose_variant(int w, bool score, Plan *pl, std::string *why)
+bool choose_variant(int w, bool score, int want_groups, Plan *pl, std::string *why)
 {
     int bits = 0, rows = 0, groups = 0;
     if (!score) {
-        if (w <= 120) {                       // 7-bit keys: w + renorm span <= 127
+        if (w <= 120 && want_groups == 2) {   // 7-bit keys, rows split over 2 threads
+            bits = 8; groups = 2; rows = (int)std::max<int64_t>(16, round_up(ceil_div(w, 2), 4));
+        } else if (w <= 120 && want_groups == 4) {
+            bits = 8; groups = 4; rows = (int)std::max<int64_t>(8, round_up(ceil_div(w, 4), 4));
+        } else if (w <= 120) {                // 7-bit keys: w + renorm span <= 127
             bits = 8; groups = 1; rows = (int)round_up(w, 8);
         } else {
             bits = 16;
@@ -71,9 +75,18 @@ bool choose_variant(int w, bool score, Plan *pl, std::string *why)
     pl->score = score;
     pl->comb_rows = score ? 2 * w : w;
     pl->max_value = score ? 2 * w : w;
-    const int half = 1 << (bits - 1);
-    pl->renorm = score ? (half - w) : (half - w) / 2;
-    pl->ring = next_pow2(w + 1);
+    // Exit ring and key range.  8-bit keys: the ring has next_pow2(2w + 2)
+    // slots (at least 32, at most 128) and keys stay below the ring size, so
+    // the kernel's exit counting needs no branch; the new key cycles through
+    // [w, ring - 1].  16-bit keys: 15-bit key range, ring = next_pow2(w + 1).
+    if (bits == 8) {
+        pl->ring = std::min(128, std::max(32, next_pow2(2 * w + 2)));
+        pl->renorm = score ? (pl->ring - w) : (pl->ring - w) / 2;
+    } else {
+        const int half = 1 << (bits - 1);
+        pl->ring = next_pow2(w + 1);
+        pl->renorm = score ? (half - w) : (half - w) / 2;
+    }
     pl->strips_per_warp = (32 / groups) * (bits == 8 ? 4 : 2);
     const int ngrp = 32 / groups;
     pl->smem = (size_t)kWarpsPerBlock * (size_t)(pl->ring * ngrp + kOB * (ngrp + 1)) * 4u;
@@ -105,6 +118,7 @@ void tile_plan(Plan *pl, int64_t rows, int64_t cols, int64_t chunk_hint, int dev
         chunk = std::max<int64_t>(chunk, round_up(16 * (int64_t)pl->w, kOB));
     }
     chunk = std::min<int64_t>(chunk, round_up(std::max<int64_t>(cols, 1), kOB));
+    chunk = std::min<int64_t>(chunk, 1LL << 30);   // tile-local indices are 32-bit
     pl->chunk = std::max<int64_t>(chunk, kOB);
     pl->nchunks = ceil_div(cols, pl->chunk);
     pl->ntiles = pl->nsg * pl->nchunks;
@@ -126,14 +140,14 @@ cudaError_t launch_comb(const Plan &pl, const uint8_t *x, int64_t m, const uint8
     static std::mutex mu;
     {
         // Raise the dynamic shared-memory limit of this kernel once per device.
-        static bool done[64][16] = {};
+        static bool done[512][16] = {};
         int dev = 0;
         cudaGetDevice(&dev);
         int count = 0;
         const Variant *t = variant_table(&count);
         const int vi = (int)(pl.v - t);
         std::lock_guard<std::mutex> lk(mu);
-        if (dev < 16 && vi < 64 && !done[vi][dev]) {
+        if (dev < 16 && vi < 512 && !done[vi][dev]) {
             cudaError_t e = cudaFuncSetAttribute((const void *)pl.v->fn,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  96 * 1024);
@@ -161,6 +175,11 @@ cudaError_t launch_comb(const Plan &pl, const uint8_t *x, int64_t m, const uint8
     p.vec_ok = (out_bytes == 1) ? ((a % 4 == 0) && (ld % 4 == 0))
                                 : ((a % 8 == 0) && (ld % 4 == 0));
     p.ring = pl.ring;
+    p.one = 1u;
+    p.shmul[0] = 1u;
+    p.shmul[1] = 1u << 24;
+    p.shmul[2] = 1u << 16;
+    p.shmul[3] = 1u << 8;
     const int64_t blocks = ceil_div(pl.ntiles, kWarpsPerBlock);
     // grid.x is limited to 2^31 - 1 blocks; split very large launches.
     const int64_t max_blocks = 1LL << 30;

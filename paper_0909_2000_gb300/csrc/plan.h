@@ -22,9 +22,10 @@ struct Plan {
     int max_value = 0;    // largest plot value: w or 2w
 };
 
-// Picks the variant for (w, score).  Returns false (with a message) when no
-// compiled variant covers it.
-bool choose_variant(int w, bool score, Plan *pl, std::string *why);
+// Picks the variant for (w, score).  `groups` > 0 asks for that many
+// threads per strip group (when a variant exists).  Returns false (with a
+// message) when no compiled variant covers the request.
+bool choose_variant(int w, bool score, int groups, Plan *pl, std::string *why);
 
 // Tiles a rows x cols plot for the chosen variant.  `chunk_hint` > 0 forces
 // the column chunk (rounded up to a multiple of 32).

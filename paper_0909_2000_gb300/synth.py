@@ -173,6 +173,14 @@ def dna_plot_100k(seed: int = 0, m: int = 100_000, n: int = 100_000, w: int = 10
     return Pair(x, y, w, (1, 0), 80, "lcs_dna_100k_w100", placed)
 
 
+def dna_plot_20k(seed: int = 0) -> Pair:
+    """The 100k DNA recipe at m = n = 20,000 (4 planted segments), w = 100:
+    a smaller case of the same kernel for profiler captures."""
+    c = dna_plot_100k(seed, 20_000, 20_000, 100, 4, 2000)
+    c.name = "lcs_dna_20k_w100"
+    return c
+
+
 def protein_score_20k(seed: int = 0, m: int = 20_000, n: int = 20_000, w: int = 64) -> Pair:
     """Score plot (match 2, mismatch 1, gap 0), uniform 20-letter protein,
     m = n = 20,000, w = 64, uint16 output."""
