@@ -192,6 +192,37 @@ ap_status ap_plot_dots(const void *plot, int32_t elem_bytes, int64_t rows,
                        ap_dot *dots, int64_t cap, int64_t *count,
                        void *workspace, int64_t workspace_bytes, void *stream);
 
+/* Largest plot height that ap_plot_dots_noalloc accepts. */
+#define AP_PLOT_DOTS_NOALLOC_MAX_ROWS 262144
+
+/*
+ * ap_plot_dots with no workspace argument and no device allocation.  The
+ * paper has no counterpart; this is an interface convenience.
+ *
+ * It is for callers that cannot call cudaMalloc, for instance a plug-in
+ * running inside a host program that owns the GPU's memory budget, or a
+ * service that must not allocate once it has started.  The scratch that
+ * ap_plot_dots takes from the caller (12 bytes per plot row: a row count, a
+ * row offset, plus a running total) lives in one fixed static device array
+ * in the library.  It is sized for AP_PLOT_DOTS_NOALLOC_MAX_ROWS rows (about
+ * 3 MiB), and every GPU that loads the library holds it until the process
+ * exits.  Taller plots are rejected with AP_E_NOMEM.
+ *
+ * The first call on a device looks up the array's address on that device
+ * (the device current at the call); make that first call before any stream
+ * capture.  All calls share the one array, which keeps the last call's
+ * contents.  Each call clears what must start at zero, but calls whose GPU
+ * work overlaps (different streams or host threads) race on the array, so
+ * the caller must order them.
+ *
+ * Arguments, results, dot order and the overflow rule are those of
+ * ap_plot_dots.  Synchronises `stream` before returning.
+ */
+ap_status ap_plot_dots_noalloc(const void *plot, int32_t elem_bytes,
+                               int64_t rows, int64_t cols, int64_t ld,
+                               int32_t threshold, ap_dot *dots, int64_t cap,
+                               int64_t *count, void *stream);
+
 /*
  * Checksum and value histogram of a plot in device memory, for checking
  * large plots without copying them:

@@ -74,6 +74,7 @@ def _declare(lib):
         "ap_plot_dots_workspace_size": [i64, i64p],
         "ap_plot_dots": [p, i32, i64, i64, i64, i32, p, i64, i64p, p, i64, p],
         "ap_plot_checksum": [p, i32, i64, i64, i64, i32, u64p, p],
+        "ap_plot_dots_noalloc": [p, i32, i64, i64, i64, i32, p, i64, i64p, p],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -270,6 +271,31 @@ def plot_dots(plot, threshold: int, cap: int | None = None, dots=None, workspace
             cap = cnt.value
         dots = _dots_tensor(cap, plot.device)
     run(dots, dots.shape[0] if cap is None else cap, ())
+    return dots, cnt.value
+
+
+PLOT_DOTS_NOALLOC_MAX_ROWS = 262144
+
+
+def plot_dots_noalloc(plot, threshold: int, dots, cap: int | None = None, stream=None):
+    """Dots of a device plot through ap_plot_dots_noalloc, which takes no
+    workspace and allocates no device memory (its scratch is a fixed array in
+    the library, for plots of at most PLOT_DOTS_NOALLOC_MAX_ROWS rows).
+
+    ``dots`` is the caller's output buffer (CUDA int32 tensor of shape
+    (capacity, 3)).  Returns (dots, count); raises ApError(AP_E_OVERFLOW) if
+    the buffer is too small (the count is still reported on the error)."""
+    rows, cols = plot.shape
+    cnt = ctypes.c_int64()
+    capacity = dots.shape[0] if cap is None else cap
+    status = load().ap_plot_dots_noalloc(ctypes.c_void_p(plot.data_ptr()), plot.element_size(), rows,
+                                         cols, plot.stride(0) if rows > 1 else cols, int(threshold),
+                                         ctypes.c_void_p(dots.data_ptr()), capacity,
+                                         ctypes.byref(cnt), _stream_handle(stream))
+    if status != AP_OK:
+        err = ApError(status, load().ap_last_error().decode())
+        err.count = cnt.value
+        raise err
     return dots, cnt.value
 
 
