@@ -183,19 +183,21 @@ class Clocks:
 
 
 def profile_traffic(kernel_tag):
-    """dram bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """dram bytes per launch from the committed ncu summary (profiles/traffic.md),
+    if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
     try:
-        rec = json.load(open(path)).get(kernel_tag)
-    except (OSError, ValueError):
-        return None
-    if not rec:
+        lines = open(path).read().splitlines()
+    except OSError:
         return None
     from paper_0909_2000_gb300 import build as b
-    if rec.get("sources") != b.kernel_digest():
-        return None
-    return rec.get("dram_bytes_per_launch")
+    for line in lines:
+        f = line.split()
+        if len(f) == 4 and f[0] == "traffic:" and f[1] == kernel_tag:
+            kv = dict(t.split("=", 1) for t in f[2:])
+            if kv.get("sources") == b.kernel_digest():
+                return int(kv["dram_bytes_per_launch"])
+    return None
 
 
 # ---------------------------------------------------------------------------
@@ -260,7 +262,7 @@ def main():
     plan = ap.plot_plan(m, n, w, scores)
     x = torch.from_numpy(c.x).to(dev)
     y = torch.from_numpy(c.y).to(dev)
-    out = torch.empty((rows, cols), dtype=torch.int16 if score else torch.uint8, device=dev)
+    out = ap.empty_plot(rows, cols, torch.int16 if score else torch.uint8, dev)
     thr = c.threshold
     ws = torch.empty(max(ap.plot_dots_workspace_size(rows), 1), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -390,10 +392,11 @@ def measure_e2e(ap, c, scores, thr, dev, steps):
     hx = torch.from_numpy(c.x).pin_memory()
     hy = torch.from_numpy(c.y).pin_memory()
     dt = torch.int16 if score else torch.uint8
-    hout = torch.empty((rows, cols), dtype=dt, pin_memory=True)
+    dout = ap.empty_plot(rows, cols, dt, dev)
+    dbase = dout.as_strided((rows, dout.stride(0)), (dout.stride(0), 1))   # padded rows
+    hout = torch.empty((rows, dout.stride(0)), dtype=dt, pin_memory=True)
     dx = torch.empty(m, dtype=torch.uint8, device=dev)
     dy = torch.empty(n, dtype=torch.uint8, device=dev)
-    dout = torch.empty((rows, cols), dtype=dt, device=dev)
     ws = torch.empty(max(ap.plot_dots_workspace_size(rows), 1), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     nd_bytes = 0
@@ -407,7 +410,7 @@ def measure_e2e(ap, c, scores, thr, dev, steps):
             d, cnt = ap.plot_dots(dout, thr, workspace=ws)
             hd = d[:cnt].cpu()
             nd_bytes = cnt * 12
-        hout.copy_(dout, non_blocking=True)
+        hout.copy_(dbase, non_blocking=True)   # the padded rows, one contiguous copy
         torch.cuda.synchronize()
 
     one()
@@ -420,7 +423,7 @@ def measure_e2e(ap, c, scores, thr, dev, steps):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / steps
     return {"value": float(m) * n * w / t, "unit": "cells/s", "h2d_bytes_per_step": m + n,
-            "d2h_bytes_per_step": rows * cols * hout.element_size() + nd_bytes + 8,
+            "d2h_bytes_per_step": hout.numel() * hout.element_size() + nd_bytes + 8,
             "ms_per_step": t * 1e3, "steps": steps}
 
 

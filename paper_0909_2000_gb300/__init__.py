@@ -19,7 +19,7 @@ import threading
 
 __all__ = [
     "load", "ApError", "LCS", "SCORE", "plot_shape", "plot_plan", "alignment_plot",
-    "alignment_dots", "plot_dots", "plot_checksum", "version", "set_chunk", "set_lanes_per_strip", "DOT_DTYPE_FIELDS",
+    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "set_chunk", "set_lanes_per_strip", "DOT_DTYPE_FIELDS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -158,6 +158,15 @@ def plot_plan(m: int, n: int, w: int, scores=LCS) -> dict:
     return {f: getattr(pl, f) for f, _ in ap_plan._fields_}
 
 
+def empty_plot(rows: int, cols: int, dtype, device):
+    """Uninitialised (rows, cols) plot whose rows start on 32-element
+    boundaries (a view of a (rows, ld) tensor, ld = cols rounded up to 32), so
+    that the kernels' row stores fill whole 32-byte sectors."""
+    import torch
+    ld = (cols + 31) // 32 * 32 if cols else 0
+    return torch.empty((rows, ld), dtype=dtype, device=device)[:, :cols]
+
+
 def alignment_plot(x, y, w: int, scores=LCS, out=None, out_dtype=None, stream=None):
     """Full plot P[i, j] for 0 <= i < m-w, 0 <= j < n-w (uint8 or uint16).
 
@@ -171,7 +180,7 @@ def alignment_plot(x, y, w: int, scores=LCS, out=None, out_dtype=None, stream=No
         if out_dtype is None:
             vmax = 2 * w if sc.match == 2 else w
             out_dtype = torch.uint8 if vmax <= 255 else torch.int16
-        out = torch.empty((rows, cols), dtype=out_dtype, device=x.device)
+        out = empty_plot(rows, cols, out_dtype, x.device)
     if out.element_size() not in (1, 2) or not out.is_cuda:
         raise ValueError("out must be a CUDA tensor of 8- or 16-bit elements")
     if out.dim() != 2 or out.stride(1) != 1 or out.shape[0] < rows or out.shape[1] < cols:

@@ -9,7 +9,8 @@
 //      total, so regions processed one after another concatenate in order),
 //   3. write every row's dots at its offset; a warp scan over the lanes'
 //      hit counts ranks the dots inside each 32 x 16-byte slice of the row.
-// Rows are read with 16-byte vector loads when the plot is 16-byte aligned.
+// Rows are read with 16-byte vector loads (four in flight per thread) when
+// the plot is 16-byte aligned, and compared four bytes at a time.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -24,44 +25,88 @@ __device__ __forceinline__ int load_val(const void *plot, int64_t off)
 {
     return (int)((const T *)plot)[off];
 }
-
-// Loads VEC = 16 / sizeof(T) plot values starting at element j of row `rowp`
-// (vector load when `vec`, else element by element, with a bounds check).
+// Cells >= thr among the 16 bytes of u, as a per-lane bit mask: bit k set
+// iff element k passes (k < 16 for uint8, k < 8 for uint16).
 template <typename T>
-struct Vec16 {
-    static constexpr int VEC = 16 / (int)sizeof(T);
-    T v[VEC];
-    __device__ __forceinline__ void load(const T *rowp, int64_t j, int64_t cols, bool vec)
-    {
-        if (vec && j + VEC <= cols) {
-            const uint4 u = *(const uint4 *)(rowp + j);
-            const T *t = (const T *)&u;
+__device__ __forceinline__ uint32_t ge_mask(uint4 u, uint32_t thr)
+{
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+    uint32_t m = 0;
+    if (sizeof(T) == 1) {
+        const uint32_t t4 = thr > 255u ? 0u : thr * 0x01010101u;
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) v[k] = t[k];
-        } else {
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t ge = (thr > 255u) ? 0u : __vcmpgeu4(w[q], t4);   // 0xFF per passing byte
+            // gather the byte flags into 4 bits
+            const uint32_t b = ge & 0x01010101u;
+            m |= ((b | (b >> 7) | (b >> 14) | (b >> 21)) & 0xFu) << (4 * q);
+        }
+    } else {
+        const uint32_t t2 = thr > 65535u ? 0u : thr * 0x00010001u;
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) v[k] = (j + k < cols) ? rowp[j + k] : (T)0;
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t ge = (thr > 65535u) ? 0u : __vcmpgeu2(w[q], t2);
+            const uint32_t b = ge & 0x00010001u;
+            m |= ((b | (b >> 15)) & 0x3u) << (2 * q);
         }
     }
-};
+    return m;
+}
+
+// Elements of the 16-byte slice starting at column j, as a mask of the valid
+// ones (columns < cols); `vec` says whether whole 16-byte loads are aligned.
+template <typename T>
+__device__ __forceinline__ uint4 load16(const T *rowp, int64_t j, int64_t cols, bool vec,
+                                        uint32_t *valid)
+{
+    constexpr int VEC = 16 / (int)sizeof(T);
+    uint4 u = make_uint4(0, 0, 0, 0);
+    if (j >= cols) {
+        *valid = 0;
+        return u;
+    }
+    if (vec && j + VEC <= cols) {
+        *valid = (VEC == 16) ? 0xFFFFu : 0xFFu;
+        return *(const uint4 *)(rowp + j);
+    }
+    union {
+        uint4 u;
+        T t[VEC];
+    } w;
+    uint32_t v = 0;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        const bool in = j + k < cols;
+        w.t[k] = in ? rowp[j + k] : (T)0;
+        v |= (uint32_t)in << k;
+    }
+    *valid = v;
+    return w.u;
+}
+
+constexpr int kUnroll = 4;   // 16-byte loads in flight per thread
 
 // One warp per row: number of cells with value >= thr.
 template <typename T>
 __global__ void row_count_kernel(const void *plot, int64_t rows, int64_t cols, int64_t ld,
                                  int thr, int vec, int32_t *counts)
 {
-    constexpr int VEC = Vec16<T>::VEC;
+    constexpr int VEC = 16 / (int)sizeof(T);
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t uthr = thr < 0 ? 0u : (uint32_t)thr;
     for (int64_t i = warp; i < rows; i += nwarps) {
         const T *rowp = (const T *)plot + i * ld;
         int c = 0;
-        for (int64_t j = (int64_t)lane * VEC; j < cols; j += 32 * VEC) {
-            Vec16<T> q;
-            q.load(rowp, j, cols, vec);
+        for (int64_t j0 = 0; j0 < cols; j0 += 32 * VEC * kUnroll) {
+            uint4 u[kUnroll];
+            uint32_t valid[kUnroll];
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) c += (int)q.v[k] >= thr && j + k < cols;
+            for (int r = 0; r < kUnroll; ++r)
+                u[r] = load16<T>(rowp, j0 + (int64_t)(r * 32 + lane) * VEC, cols, vec, &valid[r]);
+#pragma unroll
+            for (int r = 0; r < kUnroll; ++r) c += __popc(ge_mask<T>(u[r], uthr) & valid[r]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -110,53 +155,64 @@ __global__ void scan_kernel(const int32_t *counts, int64_t rows, int64_t *offset
     if (tid == 0) *running = carry;
 }
 
-// One warp per row with dots: each lane takes VEC consecutive cells, a warp
-// scan of the lanes' hit counts orders the writes, so dots come out in
-// column order.  Rows without dots are skipped.
+// One warp per row with dots: each lane takes 16-byte slices, a warp scan of
+// the lanes' hit counts orders the writes, so dots come out in column order.
+// Rows without dots are skipped.
 template <typename T>
 __global__ void row_write_kernel(const void *plot, int64_t rows, int64_t cols, int64_t ld,
                                  int thr, int vec, const int32_t *counts,
                                  const int64_t *offsets, int64_t row0, ap_dot *dots, int64_t cap)
 {
-    constexpr int VEC = Vec16<T>::VEC;
+    constexpr int VEC = 16 / (int)sizeof(T);
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t uthr = thr < 0 ? 0u : (uint32_t)thr;
     for (int64_t i = warp; i < rows; i += nwarps) {
         if (counts[i] == 0) continue;
         int64_t off = offsets[i];
         if (off >= cap) continue;
         const T *rowp = (const T *)plot + i * ld;
-        for (int64_t j0 = 0; j0 < cols && off < cap; j0 += 32 * VEC) {
-            const int64_t j = j0 + (int64_t)lane * VEC;
-            Vec16<T> q;
-            q.load(rowp, j, cols, vec);
-            int c = 0;
+        for (int64_t j0 = 0; j0 < cols && off < cap; j0 += 32 * VEC * kUnroll) {
+            uint4 u[kUnroll];
+            uint32_t valid[kUnroll];
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) c += (int)q.v[k] >= thr && j + k < cols;
-            int x = c;   // inclusive scan over lanes
+            for (int r = 0; r < kUnroll; ++r)
+                u[r] = load16<T>(rowp, j0 + (int64_t)(r * 32 + lane) * VEC, cols, vec, &valid[r]);
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += t;
-            }
-            const int total = __shfl_sync(0xffffffffu, x, 31);
-            int64_t k0 = off + (x - c);
+            for (int r = 0; r < kUnroll; ++r) {
+                const uint32_t hits = ge_mask<T>(u[r], uthr) & valid[r];
+                const int c = __popc(hits);
+                int x = c;   // inclusive scan over lanes
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) {
-                if ((int)q.v[k] >= thr && j + k < cols) {
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += t;
+                }
+                const int total = __shfl_sync(0xffffffffu, x, 31);
+                int64_t k0 = off + (x - c);
+                union {
+                    uint4 u;
+                    T t[VEC];
+                } vals;
+                vals.u = u[r];
+                const int64_t jb = j0 + (int64_t)(r * 32 + lane) * VEC;
+                uint32_t hm = hits;
+                while (hm) {
+                    const int k = __ffs(hm) - 1;
+                    hm &= hm - 1;
                     if (k0 < cap) {
                         ap_dot dt;
                         dt.i = (uint32_t)(row0 + i);
-                        dt.j = (uint32_t)(j + k);
-                        dt.value = (uint16_t)q.v[k];
+                        dt.j = (uint32_t)(jb + k);
+                        dt.value = (uint16_t)vals.t[k];
                         dt.pad = 0;
                         dots[k0] = dt;
                     }
                     ++k0;
                 }
+                off += total;
             }
-            off += total;
         }
     }
 }
