@@ -235,6 +235,71 @@ ap_status ap_plot_checksum(const void *plot, int32_t elem_bytes, int64_t rows,
                            int64_t cols, int64_t ld, int32_t nbins,
                            uint64_t *result, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched plots: many independent (x, y, w) jobs, run as one CUDA graph of
+ * persistent strip-comb kernels.  Not in the paper: it is the many-pairs
+ * form of the same computation (every job's plot is exactly the plot
+ * ap_alignment_plot would write).
+ * ---------------------------------------------------------------------- */
+
+/* One plot job.  All pointers are device pointers owned by the caller; they
+ * must stay valid (and keep their contents' meaning) for as long as the
+ * batch is run.  Fields are as in ap_alignment_plot. */
+typedef struct ap_job {
+    const uint8_t *x;
+    int64_t m;
+    const uint8_t *y;
+    int64_t n;
+    int32_t w;
+    ap_scores scores;
+    void *out;
+    int32_t out_elem_bytes;
+    int64_t ld;
+} ap_job;
+
+/* Batch options; zero-initialised means automatic. */
+typedef struct ap_batch_options {
+    int32_t autotune;         /* 1: time candidate schedules per window class at
+                                 create time (runs the jobs, writing their outputs) */
+    int32_t chunk;            /* > 0: plot columns per tile for every job */
+    int32_t lanes_per_strip;  /* > 0: threads per strip group, when compiled */
+} ap_batch_options;
+
+/* What ap_batch_create chose (informational). */
+typedef struct ap_batch_info {
+    int32_t groups;           /* persistent kernels (one per comb variant) */
+    int32_t jobs;             /* jobs with a non-empty plot */
+    int64_t tiles;            /* tiles over all groups */
+    int64_t logical_cells;    /* sum over jobs of (m-w)(n-w)w */
+    int64_t physical_cells;   /* comb cell updates incl. warm-up and padding */
+    double tune_ms;           /* time spent autotuning */
+} ap_batch_info;
+
+typedef struct ap_batch ap_batch;
+
+/*
+ * Plans a batch: validates every job (the rules of ap_alignment_plot), groups
+ * the jobs by comb variant, orders each group's tiles most expensive first,
+ * optionally autotunes the chunk length and threads per strip of each window
+ * class, and captures one CUDA graph.  The graph resets a work-queue counter
+ * per group and runs one persistent kernel per group, all groups side by
+ * side.  Uses the current device.  The batch owns a little device memory (job
+ * parameters, tile lists, counters), freed by ap_batch_destroy.  Errors: those
+ * of ap_alignment_plot for the first bad job (the message names it),
+ * AP_E_INVAL for njobs < 0 or null pointers, AP_E_CUDA.
+ */
+ap_status ap_batch_create(const ap_job *jobs, int32_t njobs,
+                          const ap_batch_options *options, ap_batch **batch);
+
+/* Runs the batch's graph on `stream` (stream-ordered, asynchronous). */
+ap_status ap_batch_run(ap_batch *batch, void *stream);
+
+/* Fills `info` (host) with the batch's plan. */
+ap_status ap_batch_get_info(const ap_batch *batch, ap_batch_info *info);
+
+/* Frees the batch (after its last run has finished).  Null is a no-op. */
+ap_status ap_batch_destroy(ap_batch *batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ import threading
 
 __all__ = [
     "load", "ApError", "LCS", "SCORE", "plot_shape", "plot_plan", "alignment_plot",
-    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "set_chunk", "set_lanes_per_strip", "DOT_DTYPE_FIELDS",
+    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "set_chunk", "set_lanes_per_strip", "Batch", "DOT_DTYPE_FIELDS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -55,6 +55,23 @@ class ap_plan(ctypes.Structure):
                 ("logical_cells", ctypes.c_int64)]
 
 
+class ap_job(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("m", ctypes.c_int64), ("y", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("w", ctypes.c_int32), ("scores", ap_scores),
+                ("out", ctypes.c_void_p), ("out_elem_bytes", ctypes.c_int32), ("ld", ctypes.c_int64)]
+
+
+class ap_batch_options(ctypes.Structure):
+    _fields_ = [("autotune", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("lanes_per_strip", ctypes.c_int32)]
+
+
+class ap_batch_info(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_int32), ("jobs", ctypes.c_int32), ("tiles", ctypes.c_int64),
+                ("logical_cells", ctypes.c_int64), ("physical_cells", ctypes.c_int64),
+                ("tune_ms", ctypes.c_double)]
+
+
 def _declare(lib):
     i32, i64, p, u64p = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
     i64p = ctypes.POINTER(ctypes.c_int64)
@@ -75,6 +92,11 @@ def _declare(lib):
         "ap_plot_dots": [p, i32, i64, i64, i64, i32, p, i64, i64p, p, i64, p],
         "ap_plot_checksum": [p, i32, i64, i64, i64, i32, u64p, p],
         "ap_plot_dots_noalloc": [p, i32, i64, i64, i64, i32, p, i64, i64p, p],
+        "ap_batch_create": [ctypes.POINTER(ap_job), i32, ctypes.POINTER(ap_batch_options),
+                            ctypes.POINTER(ctypes.c_void_p)],
+        "ap_batch_run": [p, p],
+        "ap_batch_get_info": [p, ctypes.POINTER(ap_batch_info)],
+        "ap_batch_destroy": [p],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -319,3 +341,47 @@ def plot_checksum(plot, nbins: int, stream=None):
                                    _stream_handle(stream)))
     r = res.cpu().numpy().view("uint64")
     return int(r[0]), r[1:].astype("int64")
+
+
+class Batch:
+    """Many plot jobs run as one CUDA graph of persistent comb kernels
+    (ap_batch_create / ap_batch_run / ap_batch_destroy).
+
+    ``jobs``: list of (x, y, w, scores, out) with x, y 1-D uint8 CUDA tensors
+    and ``out`` a row-major 8- or 16-bit CUDA tensor of at least (m-w, n-w).
+    The tensors must stay alive and in place while the batch is used."""
+
+    def __init__(self, jobs, autotune: bool = False, chunk: int = 0, lanes_per_strip: int = 0):
+        lib = load()
+        self._keep = []
+        arr = (ap_job * max(1, len(jobs)))()
+        for k, (x, y, w, scores, out) in enumerate(jobs):
+            x, y = _dev_u8(x, "x"), _dev_u8(y, "y")
+            rows = out.shape[0]
+            arr[k] = ap_job(x.data_ptr(), x.numel(), y.data_ptr(), y.numel(), int(w), _scores(scores),
+                            out.data_ptr(), out.element_size(),
+                            out.stride(0) if rows > 1 else max(out.shape[1], 1))
+            self._keep.append((x, y, out))
+        opt = ap_batch_options(1 if autotune else 0, int(chunk), int(lanes_per_strip))
+        h = ctypes.c_void_p()
+        _check(lib.ap_batch_create(arr, len(jobs), ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(load().ap_batch_run(self._h, _stream_handle(stream)))
+
+    def info(self) -> dict:
+        inf = ap_batch_info()
+        _check(load().ap_batch_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in ap_batch_info._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ap_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -65,7 +65,7 @@ def _generate() -> list[str]:
             lines.append("    AP_VARIANT(%s, %d, %d, %d, %s, %d)," % (lanes, bits, r, g,
                                                                     "true" if score else "false", padr))
         if not part:
-            lines.append("    {0, 0, 0, false, nullptr},")
+            lines.append("    {0, 0, 0, false, nullptr, nullptr},")
         lines += ["};", "const int kNumVariants%d = %d;" % (k, len(part)), "}  // namespace ap", ""]
         paths.append(_write_if_changed(os.path.join(gen, "variants_%02d.cu" % k), "\n".join(lines)))
     table = ['#include <vector>', '#include <mutex>', '#include "variants.h"', "namespace ap {"]

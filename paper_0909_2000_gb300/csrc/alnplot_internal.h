@@ -13,6 +13,22 @@ namespace ap {
 ap_status fail(ap_status s, const char *fmt, ...);
 ap_status fail_cuda(cudaError_t e, const char *what);
 
+struct Plan;
+
+// Scores -> mode (false: LCS, true: {2,1,0}); errors for other schemes.
+ap_status score_mode(const ap_scores *sc, bool *score);
+
+// Validated plan of one plot: variant (groups > 0 requests threads per strip
+// group), tiling (chunk > 0 forces the chunk).
+ap_status plan_plot(int64_t m, int64_t n, int32_t w, const ap_scores *scores, int groups,
+                    int64_t chunk, Plan *pl);
+
+// Output-argument checks shared by the plain and batched calls.
+ap_status check_output(const Plan &pl, const void *x, const void *y, const void *out,
+                       int32_t out_elem_bytes, int64_t ld);
+
+int current_device();
+
 // Dots of a plot region [rows x cols] (ld elements per row) in row-major order,
 // appended after *running dots; *running (device) grows by the region's count.
 // counts: device, rows int32; offsets: device, rows int64.

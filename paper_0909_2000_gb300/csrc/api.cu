@@ -31,8 +31,6 @@ ap_status fail_cuda(cudaError_t e, const char *what)
     return fail(AP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-namespace {
-
 // Scores -> mode.  Normalised form: gap 0, 0 <= mismatch < match.
 ap_status score_mode(const ap_scores *sc, bool *score)
 {
@@ -56,7 +54,8 @@ int current_device()
     return dev;
 }
 
-ap_status make_plan(int64_t m, int64_t n, int32_t w, const ap_scores *scores, Plan *pl)
+ap_status plan_plot(int64_t m, int64_t n, int32_t w, const ap_scores *scores, int groups,
+                    int64_t chunk, Plan *pl)
 {
     if (w < 1) return fail(AP_E_INVAL, "w = %d: the window length must be >= 1", w);
     if (m < 0 || n < 0) return fail(AP_E_INVAL, "negative sequence length");
@@ -64,11 +63,32 @@ ap_status make_plan(int64_t m, int64_t n, int32_t w, const ap_scores *scores, Pl
     ap_status s = score_mode(scores, &score);
     if (s != AP_OK) return s;
     std::string why;
-    if (!choose_variant(w, score, g_groups_override.load(), pl, &why))
+    if (!choose_variant(w, score, groups, pl, &why))
         return fail(AP_E_UNSUPPORTED, "%s", why.c_str());
     const int64_t rows = std::max<int64_t>(0, m - w), cols = std::max<int64_t>(0, n - w);
-    tile_plan(pl, rows, cols, g_chunk_override.load(), current_device());
+    tile_plan(pl, rows, cols, chunk, current_device());
     return AP_OK;
+}
+
+ap_status check_output(const Plan &pl, const void *x, const void *y, const void *out,
+                       int32_t out_elem_bytes, int64_t ld)
+{
+    if (out_elem_bytes != 1 && out_elem_bytes != 2)
+        return fail(AP_E_INVAL, "out_elem_bytes = %d: must be 1 or 2", out_elem_bytes);
+    if (out_elem_bytes == 1 && pl.max_value > 255)
+        return fail(AP_E_INVAL, "uint8 output cannot hold values up to %d", pl.max_value);
+    if (pl.rows == 0 || pl.cols == 0) return AP_OK;   // empty plot
+    if (!x || !y || !out) return fail(AP_E_INVAL, "null pointer");
+    if (ld < pl.cols)
+        return fail(AP_E_INVAL, "ld = %lld < cols = %lld", (long long)ld, (long long)pl.cols);
+    return AP_OK;
+}
+
+namespace {
+
+ap_status make_plan(int64_t m, int64_t n, int32_t w, const ap_scores *scores, Plan *pl)
+{
+    return plan_plot(m, n, w, scores, g_groups_override.load(), g_chunk_override.load(), pl);
 }
 
 constexpr int64_t kBandBudget = 1LL << 30;   // bytes of banded plot per dots pass
@@ -176,14 +196,8 @@ ap_status ap_alignment_plot(const uint8_t *x, int64_t m, const uint8_t *y, int64
     Plan pl;
     ap_status s = make_plan(m, n, w, scores, &pl);
     if (s != AP_OK) return s;
-    if (out_elem_bytes != 1 && out_elem_bytes != 2)
-        return fail(AP_E_INVAL, "out_elem_bytes = %d: must be 1 or 2", out_elem_bytes);
-    if (out_elem_bytes == 1 && pl.max_value > 255)
-        return fail(AP_E_INVAL, "uint8 output cannot hold values up to %d", pl.max_value);
-    if (pl.rows == 0 || pl.cols == 0) return AP_OK;   // empty plot
-    if (!x || !y || !out) return fail(AP_E_INVAL, "ap_alignment_plot: null pointer");
-    if (ld < pl.cols) return fail(AP_E_INVAL, "ld = %lld < cols = %lld", (long long)ld,
-                                  (long long)pl.cols);
+    s = check_output(pl, x, y, out, out_elem_bytes, ld);
+    if (s != AP_OK || pl.rows == 0 || pl.cols == 0) return s;
     cudaError_t e = launch_comb(pl, x, m, y, n, out, out_elem_bytes, ld, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e, "strip comb launch");
     return AP_OK;

@@ -1,0 +1,400 @@
+// batch.cu -- many plot jobs as one CUDA graph of persistent comb kernels.
+//
+// The paper combs strips of one sequence pair.  A batch combs the strips of
+// many pairs, with uneven lengths and window sizes, in one graph launch:
+//   * jobs are grouped by comb variant (key width, rows per thread, threads
+//     per strip group, score mode);
+//   * every group gets a work list of tiles (job, strip group, column
+//     chunk), most expensive first, and one persistent kernel whose warps
+//     take tiles from an atomic counter until the list is empty;
+//   * the groups' kernels run side by side on forked capture streams, so one
+//     group's tail overlaps the others' work;
+//   * an optional autotuner times candidate schedules (chunk length, threads
+//     per strip) for every window class when the batch is created.
+// Each tile is combed exactly as a plain launch combs it, so every job's plot
+// is bit-identical to ap_alignment_plot's.
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "alnplot_internal.h"
+#include "plan.h"
+
+namespace ap {
+namespace {
+
+struct Group {
+    const Variant *v = nullptr;
+    std::vector<int> jobs;       // indices into ap_batch::jobs
+    int warp_words = 0;
+    size_t smem = 0;
+    int64_t ntiles = 0;
+    BatchTile *d_tiles = nullptr;
+    int blocks = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+// Process-wide cache of tuned schedules: (score, w, SMs) -> (groups, chunk).
+std::mutex g_tune_mu;
+std::map<std::tuple<bool, int, int>, std::pair<int, int64_t>> g_tuned;
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Default batch chunk: long enough that the w - 1 warm-up columns cost at
+// most ~6%, and no shorter than 2048 columns.
+int64_t default_chunk(int w) { return std::max<int64_t>(2048, (16LL * w + 31) / 32 * 32); }
+
+// Tiles of the jobs `idx` under `plans`, most expensive first.
+std::vector<BatchTile> make_tiles(const std::vector<Plan> &plans, const std::vector<int> &idx)
+{
+    struct T {
+        int64_t cost;
+        BatchTile t;
+    };
+    std::vector<T> all;
+    for (int j : idx) {
+        const Plan &pl = plans[j];
+        for (int64_t ch = 0; ch < pl.nchunks; ++ch) {
+            const int64_t cols = std::min(pl.chunk, pl.cols - ch * pl.chunk);
+            const int64_t units = cols + pl.w - 1;
+            const int64_t cost = units * (int64_t)pl.v->rows * (pl.score ? 2 : 1);
+            for (int64_t sg = 0; sg < pl.nsg; ++sg)
+                all.push_back({cost, BatchTile{j, (int32_t)sg, (int32_t)ch, 0}});
+        }
+    }
+    std::stable_sort(all.begin(), all.end(), [](const T &a, const T &b) { return a.cost > b.cost; });
+    std::vector<BatchTile> out(all.size());
+    for (size_t i = 0; i < all.size(); ++i) out[i] = all[i].t;
+    return out;
+}
+
+int resident_blocks(const Variant *v, size_t smem)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)v->batch_fn,
+                                                      kWarpsPerBlock * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return std::max(1, per_sm) * std::max(1, sms);
+}
+
+}  // namespace
+}  // namespace ap
+
+using namespace ap;
+
+struct ap_batch {
+    int device = -1;
+    std::vector<ap_job> jobs;
+    std::vector<Plan> plans;
+    std::vector<Group> groups;
+    CombParams *d_params = nullptr;
+    unsigned int *d_next = nullptr;
+    cudaStream_t capture = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ap_batch_info info{};
+};
+
+namespace {
+
+void release(ap_batch *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto &g : b->groups) {
+        if (g.d_tiles) cudaFree(g.d_tiles);
+        if (g.stream) cudaStreamDestroy(g.stream);
+        if (g.done) cudaEventDestroy(g.done);
+    }
+    if (b->d_params) cudaFree(b->d_params);
+    if (b->d_next) cudaFree(b->d_next);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    delete b;
+}
+
+// Upload a group's tile list and size its persistent grid.
+cudaError_t prepare_group(Group &g, const std::vector<Plan> &plans)
+{
+    g.warp_words = 0;
+    for (int j : g.jobs) g.warp_words = std::max(g.warp_words, plans[j].warp_words);
+    g.smem = (size_t)kWarpsPerBlock * (size_t)g.warp_words * 4u;
+    std::vector<BatchTile> tiles = make_tiles(plans, g.jobs);
+    g.ntiles = (int64_t)tiles.size();
+    if (g.d_tiles) cudaFree(g.d_tiles);
+    g.d_tiles = nullptr;
+    if (g.ntiles == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&g.d_tiles, sizeof(BatchTile) * tiles.size());
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(g.d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(),
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    e = raise_smem_limit((const void *)g.v->batch_fn);
+    if (e != cudaSuccess) return e;
+    g.blocks = (int)std::min<int64_t>(ceil_div(g.ntiles, kWarpsPerBlock),
+                                      resident_blocks(g.v, g.smem));
+    return cudaSuccess;
+}
+
+cudaError_t launch_group(const Group &g, const CombParams *d_params, unsigned int *counter,
+                         cudaStream_t st)
+{
+    if (g.ntiles == 0) return cudaSuccess;
+    BatchParams bp;
+    bp.jobs = d_params;
+    bp.tiles = g.d_tiles;
+    bp.ntiles = g.ntiles;
+    bp.next = counter;
+    bp.warp_words = g.warp_words;
+    g.v->batch_fn<<<g.blocks, kWarpsPerBlock * 32, g.smem, st>>>(bp);
+    return cudaGetLastError();
+}
+
+cudaError_t upload_params(ap_batch *b)
+{
+    std::vector<CombParams> hp(b->jobs.size());
+    for (size_t j = 0; j < b->jobs.size(); ++j) {
+        const ap_job &jb = b->jobs[j];
+        fill_params(b->plans[j], jb.x, jb.m, jb.y, jb.n, jb.out, jb.out_elem_bytes, jb.ld, &hp[j]);
+    }
+    if (!b->d_params) {
+        cudaError_t e = cudaMalloc(&b->d_params, sizeof(CombParams) * std::max<size_t>(1, hp.size()));
+        if (e != cudaSuccess) return e;
+    }
+    if (hp.empty()) return cudaSuccess;
+    return cudaMemcpy(b->d_params, hp.data(), sizeof(CombParams) * hp.size(), cudaMemcpyHostToDevice);
+}
+
+// Autotune one window class: try (threads per strip, chunk) candidates on the
+// class's jobs, timing one persistent launch each; returns the fastest.
+ap_status tune_class(ap_batch *b, const std::vector<int> &idx, bool score, int w,
+                     std::pair<int, int64_t> *best, double *tune_ms)
+{
+    std::vector<int> groups_c = {0};
+    if (!score && w <= 120) groups_c = {1, 2};
+    std::vector<int64_t> chunks_c = {1024, 4096, 16384};
+    float best_ms = 1e30f;
+    *best = {0, default_chunk(w)};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int gc : groups_c) {
+        for (int64_t cc : chunks_c) {
+            if (cc < 4LL * w) continue;
+            std::vector<Plan> saved;
+            for (int j : idx) {
+                saved.push_back(b->plans[j]);
+                const ap_job &jb = b->jobs[j];
+                ap_status s = plan_plot(jb.m, jb.n, jb.w, &jb.scores, gc, cc, &b->plans[j]);
+                if (s != AP_OK) return s;
+            }
+            if (b->plans[idx[0]].v->groups != (gc ? gc : b->plans[idx[0]].v->groups)) {
+                for (size_t k = 0; k < idx.size(); ++k) b->plans[idx[k]] = saved[k];
+                continue;   // no compiled variant for this request
+            }
+            Group g;
+            g.v = b->plans[idx[0]].v;
+            g.jobs = idx;
+            cudaError_t e = upload_params(b);
+            if (e == cudaSuccess) e = prepare_group(g, b->plans);
+            float ms = 0;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                e = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned int), b->capture);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, b->capture);
+                if (e == cudaSuccess) e = launch_group(g, b->d_params, b->d_next, b->capture);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, b->capture);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (g.d_tiles) cudaFree(g.d_tiles);
+            for (size_t k = 0; k < idx.size(); ++k) b->plans[idx[k]] = saved[k];
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return fail_cuda(e, "batch autotune");
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                *best = {gc, cc};
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *tune_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return AP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ap_status ap_batch_create(const ap_job *jobs, int32_t njobs, const ap_batch_options *options,
+                          ap_batch **out)
+{
+    if (!out) return fail(AP_E_INVAL, "ap_batch_create: null output pointer");
+    *out = nullptr;
+    if (njobs < 0 || (njobs > 0 && !jobs)) return fail(AP_E_INVAL, "ap_batch_create: bad job list");
+    ap_batch_options opt{};
+    if (options) opt = *options;
+    if (opt.chunk < 0 || opt.lanes_per_strip < 0)
+        return fail(AP_E_INVAL, "ap_batch_create: negative option");
+    ap_batch *b = new ap_batch();
+    b->device = current_device();
+
+    // Validate and plan every job (jobs with an empty plot are dropped).
+    for (int32_t j = 0; j < njobs; ++j) {
+        const ap_job &jb = jobs[j];
+        Plan pl;
+        ap_status s = plan_plot(jb.m, jb.n, jb.w, &jb.scores, opt.lanes_per_strip,
+                                opt.chunk > 0 ? opt.chunk : default_chunk(jb.w), &pl);
+        if (s == AP_OK) s = check_output(pl, jb.x, jb.y, jb.out, jb.out_elem_bytes, jb.ld);
+        if (s != AP_OK) {
+            std::string msg = "job " + std::to_string(j) + ": " + ap_last_error();
+            release(b);
+            return fail(s, "%s", msg.c_str());
+        }
+        if (pl.ntiles == 0) continue;
+        b->jobs.push_back(jb);
+        b->plans.push_back(pl);
+    }
+
+    cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(unsigned int) * 256);
+    if (e != cudaSuccess) {
+        release(b);
+        return fail_cuda(e, "ap_batch_create");
+    }
+
+    // Autotune each window class (score mode, w), unless fixed by options.
+    if (opt.autotune && opt.chunk == 0 && opt.lanes_per_strip == 0) {
+        std::map<std::pair<bool, int>, std::vector<int>> classes;
+        for (size_t j = 0; j < b->jobs.size(); ++j)
+            classes[{b->plans[j].score, b->plans[j].w}].push_back((int)j);
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, std::max(0, b->device));
+        for (auto &kv : classes) {
+            const auto key = std::make_tuple(kv.first.first, kv.first.second, sms);
+            std::pair<int, int64_t> best;
+            bool cached = false;
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_tuned.find(key);
+                if (it != g_tuned.end()) {
+                    best = it->second;
+                    cached = true;
+                }
+            }
+            if (!cached) {
+                ap_status s = tune_class(b, kv.second, kv.first.first, kv.first.second, &best,
+                                         &b->info.tune_ms);
+                if (s != AP_OK) {
+                    release(b);
+                    return s;
+                }
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tuned[key] = best;
+            }
+            for (int j : kv.second) {
+                const ap_job &jb = b->jobs[j];
+                ap_status s = plan_plot(jb.m, jb.n, jb.w, &jb.scores, best.first, best.second,
+                                        &b->plans[j]);
+                if (s != AP_OK) {
+                    release(b);
+                    return s;
+                }
+            }
+        }
+    }
+
+    // Groups: one per comb variant, largest total work first.
+    std::map<const Variant *, std::vector<int>> by_variant;
+    for (size_t j = 0; j < b->jobs.size(); ++j) by_variant[b->plans[j].v].push_back((int)j);
+    for (auto &kv : by_variant) {
+        Group g;
+        g.v = kv.first;
+        g.jobs = kv.second;
+        b->groups.push_back(g);
+    }
+    if (b->groups.size() > 256) {
+        release(b);
+        return fail(AP_E_UNSUPPORTED, "more than 256 comb variants in one batch");
+    }
+    e = upload_params(b);
+    for (auto &g : b->groups) {
+        if (e == cudaSuccess) e = prepare_group(g, b->plans);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+    }
+    std::stable_sort(b->groups.begin(), b->groups.end(),
+                     [](const Group &a, const Group &c) { return a.ntiles > c.ntiles; });
+
+    // Capture: reset the counters, fork one stream per group, join.
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t ce = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned int) * b->groups.size(),
+                                         b->capture);
+        if (ce == cudaSuccess) ce = cudaEventRecord(b->fork, b->capture);
+        for (size_t k = 0; k < b->groups.size() && ce == cudaSuccess; ++k) {
+            Group &g = b->groups[k];
+            ce = cudaStreamWaitEvent(g.stream, b->fork, 0);
+            if (ce == cudaSuccess) ce = launch_group(g, b->d_params, b->d_next + k, g.stream);
+            if (ce == cudaSuccess) ce = cudaEventRecord(g.done, g.stream);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->capture, g.done, 0);
+        }
+        e = cudaStreamEndCapture(b->capture, &b->graph);
+        if (ce != cudaSuccess) e = ce;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        release(b);
+        return fail_cuda(e, "ap_batch_create");
+    }
+
+    b->info.groups = (int32_t)b->groups.size();
+    b->info.jobs = (int32_t)b->jobs.size();
+    for (auto &g : b->groups) b->info.tiles += g.ntiles;
+    for (size_t j = 0; j < b->jobs.size(); ++j) {
+        const Plan &pl = b->plans[j];
+        b->info.logical_cells += pl.rows * pl.cols * (int64_t)pl.w;
+        b->info.physical_cells += physical_cells(pl);
+    }
+    *out = b;
+    return AP_OK;
+}
+
+ap_status ap_batch_run(ap_batch *b, void *stream)
+{
+    if (!b) return fail(AP_E_INVAL, "ap_batch_run: null batch");
+    if (!b->exec) return AP_OK;
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail_cuda(e, "ap_batch_run");
+    return AP_OK;
+}
+
+ap_status ap_batch_get_info(const ap_batch *b, ap_batch_info *info)
+{
+    if (!b || !info) return fail(AP_E_INVAL, "ap_batch_get_info: null pointer");
+    *info = b->info;
+    return AP_OK;
+}
+
+ap_status ap_batch_destroy(ap_batch *b)
+{
+    release(b);
+    return AP_OK;
+}
+
+}  // extern "C"

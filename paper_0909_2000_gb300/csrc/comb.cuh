@@ -295,8 +295,8 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
 // Threads of a strip group are skewed by one step: thread g works on unit
 // u = s - g and takes its top seaweeds from thread g-1 by warp shuffle.
 template <class L, int R, int G, bool SCORE, int PADR>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-comb_kernel(CombParams p)
+__device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64_t ch,
+                                          uint32_t *ring)
 {
     constexpr int NS = L::NS;
     constexpr int NGRP = 32 / G;
@@ -307,19 +307,11 @@ comb_kernel(CombParams p)
     static_assert(R % (SCORE ? 2 * L::RPW : L::RPW) == 0, "R must fill whole x words");
     static_assert(PADU <= RP, "padding window larger than the lane");
 
-    extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
     const int g = (G == 1) ? 0 : (lane % G);
     const int grp = lane / G;
-    const int64_t tile = p.tile0 + (int64_t)blockIdx.x * kWarpsPerBlock + wid;
-    if (tile >= p.ntiles) return;
-
-    uint32_t *ring = smem + wid * (p.ring * NGRP + kOB * (NGRP + 1));
     uint32_t *stage = ring + p.ring * NGRP;
 
-    const int64_t sg = tile % p.nsg;
-    const int64_t ch = tile / p.nsg;
     const int64_t iw = sg * SPW;                  // first strip of the warp
     const int64_t ig = iw + (int64_t)grp * NS;    // first strip of the group
     const int64_t c0 = ch * p.chunk;
@@ -559,6 +551,65 @@ comb_kernel(CombParams p)
             }
             if (ubot >= 0) maybe_flush(ubot);
         }
+    }
+}
+
+// Shared-memory words one warp needs for a tile: the exit ring plus the
+// output stage.
+template <int G>
+__host__ __device__ constexpr int comb_warp_words(int ring)
+{
+    return ring * (32 / G) + kOB * (32 / G + 1);
+}
+
+// Plain launch: one warp per tile; tiles are numbered strip group fastest.
+template <class L, int R, int G, bool SCORE, int PADR>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+comb_kernel(CombParams p)
+{
+    extern __shared__ uint32_t smem[];
+    const int wid = threadIdx.x >> 5;
+    const int64_t tile = p.tile0 + (int64_t)blockIdx.x * kWarpsPerBlock + wid;
+    if (tile >= p.ntiles) return;
+    comb_tile<L, R, G, SCORE, PADR>(p, tile % p.nsg, tile / p.nsg,
+                                    smem + wid * comb_warp_words<G>(p.ring));
+}
+
+// One tile of a batch: which job, and which strip group and column chunk.
+struct BatchTile {
+    int32_t job;
+    int32_t sg;
+    int32_t ch;
+    int32_t pad;
+};
+
+struct BatchParams {
+    const CombParams *jobs;       // per-job parameters (device)
+    const BatchTile *tiles;       // work list, most expensive first (device)
+    int64_t ntiles;
+    unsigned int *next;           // work-queue counter, zero at launch (device)
+    int32_t warp_words;           // shared-memory words per warp
+};
+
+// Persistent launch over a batch: every warp takes the next tile of the work
+// list until it is exhausted.  Each tile is combed exactly as a plain launch
+// combs it, so results are bit-identical to one call per job.
+template <class L, int R, int G, bool SCORE, int PADR>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+comb_batch_kernel(BatchParams b)
+{
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    uint32_t *wsm = smem + wid * b.warp_words;
+    for (;;) {
+        unsigned int t = 0;
+        if (lane == 0) t = atomicAdd(b.next, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if ((int64_t)t >= b.ntiles) break;
+        const BatchTile bt = b.tiles[t];
+        comb_tile<L, R, G, SCORE, PADR>(b.jobs[bt.job], bt.sg, bt.ch, wsm);
+        __syncwarp();
     }
 }
 

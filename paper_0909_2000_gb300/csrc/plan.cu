@@ -2,6 +2,8 @@
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "plan.h"
 
@@ -90,6 +92,7 @@ bool choose_variant(int w, bool score, int want_groups, Plan *pl, std::string *w
     pl->strips_per_warp = (32 / groups) * (bits == 8 ? 4 : 2);
     const int ngrp = 32 / groups;
     pl->smem = (size_t)kWarpsPerBlock * (size_t)(pl->ring * ngrp + kOB * (ngrp + 1)) * 4u;
+    pl->warp_words = pl->ring * ngrp + kOB * (ngrp + 1);
     return true;
 }
 
@@ -133,53 +136,58 @@ int64_t physical_cells(const Plan &pl)
     return pl.nsg * (int64_t)pl.strips_per_warp * cols_phys * comb_rows_padded;
 }
 
+void fill_params(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y, int64_t n,
+                 void *out, int out_bytes, int64_t ld, CombParams *p)
+{
+    p->x = x;
+    p->y = y;
+    p->m = m;
+    p->n = n;
+    p->w = pl.w;
+    p->renorm = pl.renorm;
+    p->rows = pl.rows;
+    p->cols = pl.cols;
+    p->chunk = pl.chunk;
+    p->nsg = pl.nsg;
+    p->ntiles = pl.ntiles;
+    p->tile0 = 0;
+    p->out = out;
+    p->ld = ld;
+    p->out_bytes = out_bytes;
+    const uintptr_t a = (uintptr_t)out;
+    p->vec_ok = (out_bytes == 1) ? ((a % 4 == 0) && (ld % 4 == 0))
+                                 : ((a % 8 == 0) && (ld % 4 == 0));
+    p->ring = pl.ring;
+    p->one = 1u;
+    p->shmul[0] = 1u;
+    p->shmul[1] = 1u << 24;
+    p->shmul[2] = 1u << 16;
+    p->shmul[3] = 1u << 8;
+}
+
+cudaError_t raise_smem_limit(const void *fn)
+{
+    // Raise a kernel's dynamic shared-memory limit once per device.
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &d : done)
+        if (d.first == fn && d.second == dev) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (e == cudaSuccess) done.emplace_back(fn, dev);
+    return e;
+}
+
 cudaError_t launch_comb(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y,
                         int64_t n, void *out, int out_bytes, int64_t ld, cudaStream_t stream)
 {
     if (pl.ntiles == 0) return cudaSuccess;
-    static std::mutex mu;
-    {
-        // Raise the dynamic shared-memory limit of this kernel once per device.
-        static bool done[512][16] = {};
-        int dev = 0;
-        cudaGetDevice(&dev);
-        int count = 0;
-        const Variant *t = variant_table(&count);
-        const int vi = (int)(pl.v - t);
-        std::lock_guard<std::mutex> lk(mu);
-        if (dev < 16 && vi < 512 && !done[vi][dev]) {
-            cudaError_t e = cudaFuncSetAttribute((const void *)pl.v->fn,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 96 * 1024);
-            if (e != cudaSuccess) return e;
-            done[vi][dev] = true;
-        }
-    }
+    cudaError_t e0 = raise_smem_limit((const void *)pl.v->fn);
+    if (e0 != cudaSuccess) return e0;
     CombParams p;
-    p.x = x;
-    p.y = y;
-    p.m = m;
-    p.n = n;
-    p.w = pl.w;
-    p.renorm = pl.renorm;
-    p.rows = pl.rows;
-    p.cols = pl.cols;
-    p.chunk = pl.chunk;
-    p.nsg = pl.nsg;
-    p.ntiles = pl.ntiles;
-    p.tile0 = 0;
-    p.out = out;
-    p.ld = ld;
-    p.out_bytes = out_bytes;
-    const uintptr_t a = (uintptr_t)out;
-    p.vec_ok = (out_bytes == 1) ? ((a % 4 == 0) && (ld % 4 == 0))
-                                : ((a % 8 == 0) && (ld % 4 == 0));
-    p.ring = pl.ring;
-    p.one = 1u;
-    p.shmul[0] = 1u;
-    p.shmul[1] = 1u << 24;
-    p.shmul[2] = 1u << 16;
-    p.shmul[3] = 1u << 8;
+    fill_params(pl, x, m, y, n, out, out_bytes, ld, &p);
     const int64_t blocks = ceil_div(pl.ntiles, kWarpsPerBlock);
     // grid.x is limited to 2^31 - 1 blocks; split very large launches.
     const int64_t max_blocks = 1LL << 30;

@@ -19,6 +19,7 @@ struct Plan {
     int64_t rows = 0, cols = 0;
     int64_t chunk = 0, nchunks = 0, nsg = 0, ntiles = 0;
     size_t smem = 0;      // dynamic shared memory per block
+    int warp_words = 0;   // shared-memory words per warp
     int max_value = 0;    // largest plot value: w or 2w
 };
 
@@ -30,6 +31,13 @@ bool choose_variant(int w, bool score, int groups, Plan *pl, std::string *why);
 // Tiles a rows x cols plot for the chosen variant.  `chunk_hint` > 0 forces
 // the column chunk (rounded up to a multiple of 32).
 void tile_plan(Plan *pl, int64_t rows, int64_t cols, int64_t chunk_hint, int device);
+
+// Kernel parameters of one plot (shared by plain and batched launches).
+void fill_params(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y, int64_t n,
+                 void *out, int out_bytes, int64_t ld, CombParams *p);
+
+// Raises a kernel's dynamic shared-memory limit (once per kernel and device).
+cudaError_t raise_smem_limit(const void *fn);
 
 // Launch one comb over `pl` on `stream`.
 cudaError_t launch_comb(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y,

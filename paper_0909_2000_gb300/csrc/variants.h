@@ -9,6 +9,7 @@
 namespace ap {
 
 typedef void (*comb_fn_t)(CombParams);
+typedef void (*batch_fn_t)(BatchParams);
 
 struct Variant {
     int lane_bits;   // 8 or 16
@@ -16,6 +17,7 @@ struct Variant {
     int groups;      // G: threads per strip group
     bool score;      // '$'-interleaved strings
     comb_fn_t fn;
+    batch_fn_t batch_fn;
 };
 
 // Filled by the instantiation units (variants_*.cu).
@@ -25,4 +27,5 @@ const Variant *variant_table(int *count);
 
 // Instantiation helper: one template instance plus its registry entry.
 #define AP_VARIANT(LANES, BITS, R, G, SCORE, PADR)                                  \
-    { BITS, R, G, SCORE, &ap::comb_kernel<ap::LANES, R, G, SCORE, PADR> }
+    { BITS, R, G, SCORE, &ap::comb_kernel<ap::LANES, R, G, SCORE, PADR>,                \
+      &ap::comb_batch_kernel<ap::LANES, R, G, SCORE, PADR> }

@@ -91,29 +91,32 @@ def mutate(src: np.ndarray, seed: int, stream: int, alphabet, sub: float,
            indel: float) -> np.ndarray:
     """Copy of ``src`` with substitutions (to a different letter, rate ``sub``)
     and single-character indels (rate ``indel``, half insertions, half
-    deletions)."""
+    deletions).  Position p draws u[p]: u < sub substitutes, the next indel/2
+    inserts a random letter before the character, the next indel/2 deletes
+    it, anything else copies it."""
     alphabet = np.asarray(alphabet, dtype=np.uint8)
     sigma = len(alphabet)
     code = np.full(256, -1, dtype=np.int64)
     code[alphabet] = np.arange(sigma)
+    src = np.asarray(src, dtype=np.uint8)
     L = len(src)
     u = uniform01(seed, stream, L)
     r = below(seed, stream + 1, L, max(1, sigma - 1))
     ins = below(seed, stream + 2, L, sigma)
-    out = []
-    for p in range(L):
-        c = int(src[p])
-        if u[p] < sub:
-            k = code[c] if code[c] >= 0 else 0
-            out.append(int(alphabet[(k + 1 + r[p]) % sigma]))
-        elif u[p] < sub + indel / 2:          # insertion before the character
-            out.append(int(alphabet[ins[p]]))
-            out.append(c)
-        elif u[p] < sub + indel:              # deletion
-            pass
-        else:
-            out.append(c)
-    return np.asarray(out, dtype=np.uint8)
+    k = np.maximum(code[src], 0)
+    subst = alphabet[(k + 1 + r) % sigma]
+    is_sub = u < sub
+    is_ins = (~is_sub) & (u < sub + indel / 2)
+    is_del = (~is_sub) & (~is_ins) & (u < sub + indel)
+    body = np.where(is_sub, subst, src)              # the character each position keeps
+    lens = np.where(is_del, 0, np.where(is_ins, 2, 1))
+    out = np.empty(int(lens.sum()), dtype=np.uint8)
+    start = np.cumsum(lens) - lens                   # first output slot of each position
+    keep = ~is_del
+    # the kept character is the last slot of its position
+    out[(start + lens - 1)[keep]] = body[keep]
+    out[start[is_ins]] = alphabet[ins[is_ins]]
+    return out
 
 
 def plant(x: np.ndarray, y: np.ndarray, count: int, length: int, seed: int,
