@@ -47,7 +47,10 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lcs_dna_100k_w100",
                     choices=["lcs_dna_100k_w100", "lcs_dna_512_w16", "score_protein_20k_w64",
-                             "lcs_dna_20k_w100", "batch_dna_4096"])
+                             "lcs_dna_20k_w100", "batch_dna_4096", "serve_dna_poisson"])
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -344,12 +347,105 @@ def bench_batch(args):
     return 0 if (same and ok) else 1
 
 
+def bench_serve(args):
+    """Open-loop Poisson arrivals of DNA dot-plot requests (m, n log-uniform
+    1000..200000, w uniform in {32,64,128,256}, dots >= ceil(0.8 w)) into the
+    server; p50/p99 latency, throughput, offered load; then the same at a rate
+    the GPU sustains; and a loop of plain dots calls for comparison."""
+    import threading as th
+
+    import numpy as np
+    import torch
+
+    import paper_0909_2000_gb300 as ap
+    from paper_0909_2000_gb300 import synth
+
+    ap.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+
+    def cells(p):
+        return float(max(0, len(p.x) - p.w)) * max(0, len(p.y) - p.w) * p.w
+
+    def run(rate, seconds, seed):
+        reqs = synth.serving_requests(seed, rate=rate, duration=seconds)
+        srv = ap.Server(mem_budget=64 << 30, max_slots=args.serve_slots)
+        tickets = [None] * len(reqs)
+        t0 = time.perf_counter()
+
+        def submitter():
+            for k, (at, p) in enumerate(reqs):
+                dt = at - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[k] = srv.submit(p.x, p.y, p.w, p.threshold, max_dots=1 << 24)
+
+        thr = th.Thread(target=submitter)
+        thr.start()
+        thr.join()
+        statuses = []
+        ndots = 0
+        for t in tickets:
+            statuses.append(srv.wait(t, -1))
+            st, cnt, _ = srv.fetch(t, cap=0)
+            ndots += cnt
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        total = sum(cells(p) for _, p in reqs)
+        return {"rate_req_s": rate, "arrival_seconds": seconds, "requests": len(reqs),
+                "offered_cells_per_s": total / seconds, "completed": stats["completed"],
+                "ok": sum(1 for s_ in statuses if s_ == ap.AP_OK), "dots": ndots,
+                "wall_s": wall, "throughput_cells_per_s": total / wall,
+                "latency_p50_ms": stats["latency_p50_ms"], "latency_p99_ms": stats["latency_p99_ms"],
+                "latency_max_ms": stats["latency_max_ms"], "peak_device_bytes": stats["peak_device_bytes"],
+                "mean_cells_per_request": total / max(1, len(reqs))}
+
+    clocks = Clocks(0)
+    clocks.start()
+    overload = run(args.serve_rate, args.serve_seconds, 0)
+    capacity = overload["throughput_cells_per_s"]
+    sust_rate = max(1.0, 0.7 * capacity / overload["mean_cells_per_request"])
+    sustained = run(sust_rate, max(10.0, args.serve_seconds), 1)
+    clk = clocks.stop()
+    # plain form: the same kind of requests, one ap_alignment_dots call after another
+    reqs = synth.serving_requests(2, rate=args.serve_rate, duration=1.0)[:60]
+    dev = torch.device("cuda", 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _, p in reqs:
+        x = torch.from_numpy(p.x).to(dev)
+        y = torch.from_numpy(p.y).to(dev)
+        ap.alignment_dots(x, y, p.w, p.threshold)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain_rate = sum(cells(p) for _, p in reqs) / plain_s
+    line = {
+        "metric": "window-pair cells/sec (m*n*w/s)", "value": sustained["throughput_cells_per_s"],
+        "unit": "cells/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8/u16 keys", "data": "synthetic",
+        "config": {"workload": "serve_dna_poisson",
+                   "requests": "Poisson arrivals; m, n log-uniform 1000..200000; w uniform in "
+                               "{32,64,128,256}; dots >= ceil(0.8 w); device budget 64 GiB, %d slots"
+                               % args.serve_slots},
+        "open_loop_at_offered_rate": overload,
+        "open_loop_at_sustainable_rate": sustained,
+        "offered_over_capacity": overload["offered_cells_per_s"] / capacity,
+        "plain_sequential_dots": {"requests": len(reqs), "cells_per_s": plain_rate},
+        "served_over_plain": capacity / plain_rate,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch_dna_4096":
         return bench_batch(args)
+    if args.workload == "serve_dna_poisson":
+        return bench_serve(args)
 
     import numpy as np
     import torch

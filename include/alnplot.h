@@ -300,6 +300,87 @@ ap_status ap_batch_get_info(const ap_batch *batch, ap_batch_info *info);
 /* Frees the batch (after its last run has finished).  Null is a no-op. */
 ap_status ap_batch_destroy(ap_batch *batch);
 
+/* ------------------------------------------------------------------------
+ * Serving: dot-plot requests from host memory, admitted by device memory
+ * and free slots, with their work overlapping on the GPU (continuous
+ * batching).  Not in the paper: it serves the same computation
+ * (ap_alignment_dots) to many clients.
+ * ---------------------------------------------------------------------- */
+
+/* One request.  x and y are HOST pointers; ap_server_submit copies them, so
+ * the caller may free them as soon as it returns.  The result is every
+ * window pair with P[i][j] >= threshold (row-major ap_dot records, as in
+ * ap_alignment_dots), at most max_dots of them; a larger count ends the job
+ * with AP_E_OVERFLOW, still reporting the full count and the first
+ * max_dots dots. */
+typedef struct ap_request {
+    const uint8_t *x;
+    int64_t m;
+    const uint8_t *y;
+    int64_t n;
+    int32_t w;
+    ap_scores scores;
+    int32_t threshold;
+    int64_t max_dots;
+} ap_request;
+
+/* Server counters (ap_server_get_stats).  Latency is from submit to the
+ * moment the result is ready, over completed jobs. */
+typedef struct ap_server_stats {
+    int64_t submitted;
+    int64_t completed;        /* finished with AP_OK or AP_E_OVERFLOW */
+    int64_t failed;           /* finished with another error or cancelled */
+    int64_t queued;           /* waiting for a slot or memory */
+    int64_t running;          /* admitted, not finished */
+    int64_t logical_cells;    /* sum of (m-w)(n-w)w over completed jobs */
+    int64_t peak_device_bytes;/* largest device memory held by admitted jobs */
+    double latency_p50_ms;
+    double latency_p99_ms;
+    double latency_max_ms;
+} ap_server_stats;
+
+typedef struct ap_server ap_server;
+
+/*
+ * Starts a server on the current device with `max_slots` concurrent jobs
+ * (1..64) and `mem_budget` bytes of device memory for admitted jobs (their
+ * sequences, plot band, row counts and dots).  A scheduler thread admits
+ * queued requests in arrival order when a slot is free and the job's memory
+ * fits the budget; each admitted job runs on its own stream, so the work of
+ * different jobs overlaps on the device.  Errors: AP_E_INVAL, AP_E_CUDA.
+ */
+ap_status ap_server_create(int64_t mem_budget, int32_t max_slots, ap_server **server);
+
+/* Queues a request and returns its ticket (> 0).  Validation errors of
+ * ap_alignment_dots are returned here; a job that can never fit the memory
+ * budget returns AP_E_NOMEM. */
+ap_status ap_server_submit(ap_server *server, const ap_request *request, uint64_t *ticket);
+
+/* State of a ticket: AP_E_BUSY while queued or running, else the job's final
+ * status (AP_OK, AP_E_OVERFLOW, AP_E_CANCELLED, AP_E_CUDA ...).  AP_E_INVAL for
+ * an unknown (or already fetched) ticket. */
+ap_status ap_server_poll(ap_server *server, uint64_t ticket, ap_status *state);
+
+/* Blocks until the job has finished or `timeout_ms` has passed (< 0: no
+ * limit).  Returns the job's final status, or AP_E_TIMEOUT. */
+ap_status ap_server_wait(ap_server *server, uint64_t ticket, int32_t timeout_ms);
+
+/* Copies a finished job's result into `dots` (HOST, room for `cap` records)
+ * and its full count into *count, then forgets the ticket.  Returns the job's
+ * final status; AP_E_BUSY if it has not finished (nothing is consumed). */
+ap_status ap_server_fetch(ap_server *server, uint64_t ticket, ap_dot *dots, int64_t cap,
+                          int64_t *count);
+
+/* Cancels a queued job (it never runs) or a running one (its result is
+ * dropped when its GPU work ends).  Its state becomes AP_E_CANCELLED. */
+ap_status ap_server_cancel(ap_server *server, uint64_t ticket);
+
+ap_status ap_server_get_stats(ap_server *server, ap_server_stats *stats);
+
+/* Stops the scheduler after the jobs already admitted have finished, drops
+ * queued ones, and frees everything.  Null is a no-op. */
+ap_status ap_server_destroy(ap_server *server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ import threading
 
 __all__ = [
     "load", "ApError", "LCS", "SCORE", "plot_shape", "plot_plan", "alignment_plot",
-    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "set_chunk", "set_lanes_per_strip", "Batch", "DOT_DTYPE_FIELDS",
+    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "set_chunk", "set_lanes_per_strip", "Batch", "Server", "DOT_DTYPE_FIELDS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -72,6 +72,20 @@ class ap_batch_info(ctypes.Structure):
                 ("tune_ms", ctypes.c_double)]
 
 
+class ap_request(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("m", ctypes.c_int64), ("y", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("w", ctypes.c_int32), ("scores", ap_scores),
+                ("threshold", ctypes.c_int32), ("max_dots", ctypes.c_int64)]
+
+
+class ap_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("logical_cells", ctypes.c_int64), ("peak_device_bytes", ctypes.c_int64),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("latency_max_ms", ctypes.c_double)]
+
+
 def _declare(lib):
     i32, i64, p, u64p = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
     i64p = ctypes.POINTER(ctypes.c_int64)
@@ -97,6 +111,14 @@ def _declare(lib):
         "ap_batch_run": [p, p],
         "ap_batch_get_info": [p, ctypes.POINTER(ap_batch_info)],
         "ap_batch_destroy": [p],
+        "ap_server_create": [i64, i32, ctypes.POINTER(ctypes.c_void_p)],
+        "ap_server_submit": [p, ctypes.POINTER(ap_request), ctypes.POINTER(ctypes.c_uint64)],
+        "ap_server_poll": [p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)],
+        "ap_server_wait": [p, ctypes.c_uint64, i32],
+        "ap_server_fetch": [p, ctypes.c_uint64, p, i64, i64p],
+        "ap_server_cancel": [p, ctypes.c_uint64],
+        "ap_server_get_stats": [p, ctypes.POINTER(ap_server_stats)],
+        "ap_server_destroy": [p],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -378,6 +400,76 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             load().ap_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Dot-plot server (ap_server_*): requests carry host sequences; results
+    come back as (k, 3) int64 arrays of (i, j, value), row-major."""
+
+    def __init__(self, mem_budget: int, max_slots: int = 8):
+        h = ctypes.c_void_p()
+        _check(load().ap_server_create(int(mem_budget), int(max_slots), ctypes.byref(h)))
+        self._h = h
+        self._max_dots = {}
+
+    def submit(self, x, y, w: int, threshold: int, scores=LCS, max_dots: int = 1 << 22) -> int:
+        import numpy as np
+        x = np.ascontiguousarray(x, dtype=np.uint8)
+        y = np.ascontiguousarray(y, dtype=np.uint8)
+        req = ap_request(x.ctypes.data, len(x), y.ctypes.data, len(y), int(w), _scores(scores),
+                         int(threshold), int(max_dots))
+        t = ctypes.c_uint64()
+        _check(load().ap_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        self._max_dots[t.value] = int(max_dots)
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        st = ctypes.c_int()
+        _check(load().ap_server_poll(self._h, ticket, ctypes.byref(st)))
+        return st.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> int:
+        """The job's final status (AP_OK, AP_E_OVERFLOW, ...) or AP_E_TIMEOUT."""
+        return load().ap_server_wait(self._h, ticket, int(timeout_ms))
+
+    def fetch(self, ticket: int, cap: int | None = None):
+        """(status, count, dots) for a finished job; dots is an (k, 3) int64
+        array with k = min(count, the job's max_dots, cap)."""
+        import numpy as np
+        lib = load()
+        cnt = ctypes.c_int64()
+        held = self._max_dots.get(ticket, 1 << 22)
+        cap = held if cap is None else min(cap, held)
+        buf = np.zeros((max(cap, 1), 3), dtype=np.uint32)
+        st = lib.ap_server_fetch(self._h, ticket, buf.ctypes.data, cap, ctypes.byref(cnt))
+        if st not in (AP_OK, AP_E_OVERFLOW, AP_E_CANCELLED, AP_E_CUDA):
+            raise ApError(st, lib.ap_last_error().decode())
+        self._max_dots.pop(ticket, None)
+        k = min(cnt.value, cap)
+        out = np.zeros((k, 3), dtype=np.int64)
+        out[:, 0] = buf[:k, 0]
+        out[:, 1] = buf[:k, 1]
+        out[:, 2] = buf[:k, 2] & 0xFFFF
+        return st, cnt.value, out
+
+    def cancel(self, ticket: int) -> None:
+        _check(load().ap_server_cancel(self._h, ticket))
+
+    def stats(self) -> dict:
+        st = ap_server_stats()
+        _check(load().ap_server_get_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ap_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ap_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
