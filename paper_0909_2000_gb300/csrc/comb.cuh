@@ -53,6 +53,9 @@
 namespace ap {
 
 constexpr int kWarpsPerBlock = 4;
+#ifndef AP_MIN_BLOCKS
+#define AP_MIN_BLOCKS 1   // minimum resident blocks per SM asked of the compiler
+#endif
 constexpr int kOB = 32;   // plot columns staged per flush (one per lane)
 
 struct CombParams {
@@ -171,7 +174,7 @@ template <class L>
 __device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t mm, uint32_t neg1)
 {
     const uint32_t hc = h | ~mm | L::MSB;
-    const uint32_t t = mad_lo(v, neg1, hc);   // hc - v
+    const uint32_t t = mad_lo(v, neg1, hc);      // hc - v
     const uint32_t M = prmt(t, 0u, L::SIGNREP);
     const uint32_t vn = (h & M) | (v & ~M);
     h = h ^ v ^ vn;
@@ -182,9 +185,9 @@ __device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t mm, uint
 template <class L>
 __device__ __forceinline__ void cell_mismatch(uint32_t &h, uint32_t &v)
 {
-    uint32_t t = h - v + L::MSB;
-    uint32_t M = prmt(t, 0u, L::SIGNREP);
-    uint32_t vn = (h & M) | (v & ~M);
+    const uint32_t t = h - v + L::MSB;
+    const uint32_t M = prmt(t, 0u, L::SIGNREP);
+    const uint32_t vn = (h & M) | (v & ~M);
     h = h ^ v ^ vn;
     v = vn;
 }
@@ -564,7 +567,7 @@ __host__ __device__ constexpr int comb_warp_words(int ring)
 
 // Plain launch: one warp per tile; tiles are numbered strip group fastest.
 template <class L, int R, int G, bool SCORE, int PADR>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, AP_MIN_BLOCKS)
 comb_kernel(CombParams p)
 {
     extern __shared__ uint32_t smem[];
@@ -595,7 +598,7 @@ struct BatchParams {
 // list until it is exhausted.  Each tile is combed exactly as a plain launch
 // combs it, so results are bit-identical to one call per job.
 template <class L, int R, int G, bool SCORE, int PADR>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, AP_MIN_BLOCKS)
 comb_batch_kernel(BatchParams b)
 {
     extern __shared__ uint32_t smem[];
