@@ -89,8 +89,9 @@ struct CombParams {
 struct U8Lanes {
     static constexpr int NS = 4;        // strips per register
     static constexpr int BITS = 8;
+    static constexpr bool FULL = false; // keys use 7 bits; bit 7 is the compare bit
     static constexpr int RPW = 4;       // rows per aligned x word
-    static constexpr int KMAX = 127;    // keys are 7-bit; bit 7 is the compare bit
+    static constexpr int KMAX = 127;
     static constexpr uint32_t ONES = 0x01010101u;
     static constexpr uint32_t MSB = 0x80808080u;
     static constexpr uint32_t LOW = 0x7F7F7F7Fu;
@@ -98,9 +99,25 @@ struct U8Lanes {
     static constexpr uint32_t MASK = 0xFFu;
 };
 
+// 8-bit lanes with full 8-bit keys (windows up to 254): compares and
+// subtractions handle the top bit separately.
+struct U8FLanes {
+    static constexpr int NS = 4;
+    static constexpr int BITS = 8;
+    static constexpr bool FULL = true;
+    static constexpr int RPW = 4;
+    static constexpr int KMAX = 255;
+    static constexpr uint32_t ONES = 0x01010101u;
+    static constexpr uint32_t MSB = 0x80808080u;
+    static constexpr uint32_t LOW = 0x7F7F7F7Fu;
+    static constexpr uint32_t SIGNREP = 0xBA98u;
+    static constexpr uint32_t MASK = 0xFFu;
+};
+
 struct U16Lanes {
     static constexpr int NS = 2;
     static constexpr int BITS = 16;
+    static constexpr bool FULL = false;
     static constexpr int RPW = 2;
     static constexpr int KMAX = 32767;
     static constexpr uint32_t ONES = 0x00010001u;
@@ -129,6 +146,24 @@ __device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
     uint32_t r;
     asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
     return r;
+}
+
+// Full-width unsigned a >= b in every lane, as the lane's top bit (other bits
+// are junk): compare the low bits with the top bit forced on a and off b (no
+// borrow between lanes), then let the top bits decide where they differ.
+template <class L>
+__device__ __forceinline__ uint32_t ge_lanes(uint32_t a, uint32_t b, uint32_t neg1)
+{
+    const uint32_t t = mad_lo(b & L::LOW, neg1, a | L::MSB);   // MSB: a_low >= b_low
+    return (a & ~b) | (~(a ^ b) & t);
+}
+
+// Lane-wise (a - b) modulo the lane width, with no borrow between lanes.
+template <class L>
+__device__ __forceinline__ uint32_t sub_lanes(uint32_t a, uint32_t b)
+{
+    const uint32_t lo = (a | L::MSB) - (b & L::LOW);
+    return lo ^ ((a ^ ~b) & L::MSB);
 }
 
 // Row register for rows r = 1..RPW-1 past an aligned word: the lanes start r
@@ -170,12 +205,22 @@ __device__ __forceinline__ uint32_t mismatch_mask(uint32_t xw, uint32_t yb, uint
 // lane, and h >= v otherwise (keys are at most 0x7F.., no borrow between
 // lanes).  hc does not depend on v, so the dependency chain from one cell to
 // the next is three instructions: subtract, sign-spread, select.
+//
+// With full 8-bit keys (U8FLanes) the top bit belongs to the key, so the
+// match is folded in as hm = 0xFF in match lanes (>= any key) and the swap
+// decision is the full-width compare hm >= v.
 template <class L>
 __device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t mm, uint32_t neg1)
 {
-    const uint32_t hc = h | ~mm | L::MSB;
-    const uint32_t t = mad_lo(v, neg1, hc);      // hc - v
-    const uint32_t M = prmt(t, 0u, L::SIGNREP);
+    uint32_t M;
+    if (L::FULL) {
+        const uint32_t hm = h | ~mm;
+        M = prmt(ge_lanes<L>(hm, v, neg1), 0u, L::SIGNREP);
+    } else {
+        const uint32_t hc = h | ~mm | L::MSB;
+        const uint32_t t = mad_lo(v, neg1, hc);  // hc - v
+        M = prmt(t, 0u, L::SIGNREP);
+    }
     const uint32_t vn = (h & M) | (v & ~M);
     h = h ^ v ^ vn;
     v = vn;
@@ -183,19 +228,25 @@ __device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t mm, uint
 
 // Mismatch cell (no match possible): swap iff h >= v.
 template <class L>
-__device__ __forceinline__ void cell_mismatch(uint32_t &h, uint32_t &v)
+__device__ __forceinline__ void cell_mismatch(uint32_t &h, uint32_t &v, uint32_t neg1)
 {
-    const uint32_t t = h - v + L::MSB;
+    const uint32_t t = L::FULL ? ge_lanes<L>(h, v, neg1) : h - v + L::MSB;
     const uint32_t M = prmt(t, 0u, L::SIGNREP);
     const uint32_t vn = (h & M) | (v & ~M);
     h = h ^ v ^ vn;
     v = vn;
 }
 
-// Keys drop by rr, saturating at 0.
+// Keys drop by rr, saturating at 0.  rr_bias = (half - rr) per lane for
+// keys below half; rrv = rr per lane for full-width keys.
 template <class L>
-__device__ __forceinline__ uint32_t renorm_key(uint32_t k, uint32_t rr_bias, uint32_t one)
+__device__ __forceinline__ uint32_t renorm_key(uint32_t k, uint32_t rr_bias, uint32_t rrv,
+                                               uint32_t one, uint32_t neg1)
 {
+    if (L::FULL) {
+        const uint32_t M = prmt(ge_lanes<L>(k, rrv, neg1), 0u, L::SIGNREP);
+        return sub_lanes<L>(k, rrv) & M;
+    }
     uint32_t t = mad_lo(k, one, rr_bias);     // lane: k + (half - rr), MSB iff k >= rr
     uint32_t M = prmt(t, 0u, L::SIGNREP);
     return t & M & L::LOW;
@@ -364,6 +415,8 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
     const uint32_t inval_bias = (uint32_t)((1u << (L::BITS - 1)) - (uint32_t)wk) * L::ONES;
     const int kdrop = SCORE ? p.renorm : 2 * p.renorm;
     const uint32_t rr_bias = (uint32_t)((1u << (L::BITS - 1)) - (uint32_t)kdrop) * L::ONES;
+    const uint32_t rrv = (uint32_t)kdrop * L::ONES;
+    const uint32_t wkv = (uint32_t)wk * L::ONES;
     const int ring_mask = p.ring - 1;
     const uint32_t ring_maskv = (uint32_t)ring_mask * L::ONES;
     const int plot_cols = (int)(c1 - c0);
@@ -396,12 +449,15 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
     uint8_t *ring8 = (uint8_t *)(ring + grp);
     auto count_exit = [&](uint32_t ex, uint32_t knew, int col) {
         const uint32_t age = knew - ex;                       // per lane, >= 0
-        const uint32_t inval = (age + inval_bias) & L::MSB;   // age >= w
+        const uint32_t inval = (L::FULL ? ge_lanes<L>(age, wkv, neg1)
+                                        : age + inval_bias) & L::MSB;   // age >= w
         const uint32_t valid = (inval ^ L::MSB) >> (L::BITS - 1);
         d += valid;
         if (L::BITS == 8) {
             const uint32_t colb = (uint32_t)(col & ring_mask) * L::ONES;
-            const uint32_t slots = (colb + L::MSB - age) & ring_maskv;   // (col - age) mod ring
+            // (col - age) mod ring per lane (the ring has 256 slots with full keys)
+            const uint32_t slots = L::FULL ? sub_lanes<L>(colb, age)
+                                           : (colb + L::MSB - age) & ring_maskv;
 #pragma unroll
             for (int b = 0; b < NS; ++b) {
                 const uint32_t slot = (slots >> (8 * b)) & (uint32_t)ring_mask;
@@ -458,7 +514,7 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
             kc += SCORE ? 1 : 2;
             if (++since == p.renorm) {     // Proposition 3.4: old keys collapse to 0
 #pragma unroll
-                for (int k = 0; k < R; ++k) h[k] = renorm_key<L>(h[k], rr_bias, one);
+                for (int k = 0; k < R; ++k) h[k] = renorm_key<L>(h[k], rr_bias, rrv, one, neg1);
                 kc = wk;
                 since = 0;
             }
@@ -516,9 +572,9 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
                     h[2 * q] = va;
                     va = tmp;
                 }
-                cell_mismatch<L>(h[2 * q + 1], va);
+                cell_mismatch<L>(h[2 * q + 1], va, neg1);
                 // character column: '$' row mismatches, x row compares.
-                cell_mismatch<L>(h[2 * q], vb);
+                cell_mismatch<L>(h[2 * q], vb, neg1);
                 const int qq = q / L::RPW, r = q % L::RPW;
                 uint32_t mq = (r == 0) ? mm[qq] : row_shift(mm[qq], mm[qq + 1], shm(r));
                 if (pi >= 0) mq |= pad;

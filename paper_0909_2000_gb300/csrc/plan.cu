@@ -14,12 +14,12 @@ namespace {
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
-const Variant *find_variant(int bits, int rows, int groups, bool score)
+const Variant *find_variant(int key_bits, int rows, int groups, bool score)
 {
     int count = 0;
     const Variant *t = variant_table(&count);
     for (int i = 0; i < count; ++i)
-        if (t[i].lane_bits == bits && t[i].rows == rows && t[i].groups == groups &&
+        if (t[i].key_bits == key_bits && t[i].rows == rows && t[i].groups == groups &&
             t[i].score == score)
             return &t[i];
     return nullptr;
@@ -36,33 +36,45 @@ int next_pow2(int v)
 
 bool choose_variant(int w, bool score, int want_groups, Plan *pl, std::string *why)
 {
-    int bits = 0, rows = 0, groups = 0;
+    // key_bits: 7 (w <= 120), 8 (LCS, w <= 254: values fit a byte), else 15.
+    int kbits = 0, rows = 0, groups = 0;
+    auto rows_for = [&](int g, int unit, int lo, int hi) -> bool {
+        // rows per thread for g threads: units (rows or pairs) rounded up to a
+        // multiple of `unit`, at least lo; false if above hi
+        int64_t r = std::max<int64_t>(lo, round_up(ceil_div(w, g), unit));
+        if (r > hi) return false;
+        groups = g;
+        rows = (int)r;
+        return true;
+    };
     if (!score) {
-        if (w <= 120 && want_groups == 2) {   // 7-bit keys, rows split over 2 threads
-            bits = 8; groups = 2; rows = (int)std::max<int64_t>(16, round_up(ceil_div(w, 2), 4));
-        } else if (w <= 120 && want_groups == 4) {
-            bits = 8; groups = 4; rows = (int)std::max<int64_t>(8, round_up(ceil_div(w, 4), 4));
-        } else if (w <= 120) {                // 7-bit keys: w + renorm span <= 127
-            bits = 8; groups = 1; rows = (int)round_up(w, 8);
+        if (w <= 120) {
+            kbits = 7;
+            if (want_groups == 2) rows_for(2, 4, 16, 60);
+            else if (want_groups == 4) rows_for(4, 4, 8, 32);
+            if (!rows) rows_for(1, 8, 8, 120);
+        } else if (w <= 254) {
+            kbits = 8;
+            if (want_groups == 4 || !rows_for(2, 64, 64, 64)) rows_for(4, 4, 32, 64);
         } else {
-            bits = 16;
-            for (int g : {2, 4, 8}) {
-                int r = (int)std::max<int64_t>(16, round_up(ceil_div(w, g), 8));
-                if (r <= 64) { groups = g; rows = r; break; }
-            }
+            kbits = 15;
+            for (int g : {2, 4, 8})
+                if (rows_for(g, 8, 16, 64)) break;
         }
     } else {
         if (w <= 64) {
-            bits = 8; groups = 1; rows = 2 * (int)round_up(w, 4);
+            kbits = 7;
+            if (rows_for(1, 4, 4, 64)) rows *= 2;
         } else if (w <= 120) {
-            bits = 8; groups = 2; rows = 2 * (int)round_up(ceil_div(w, 2), 4);
+            kbits = 7;
+            if (rows_for(2, 4, 36, 60)) rows *= 2;
         } else {
-            bits = 16; groups = 8;
-            int rp = (int)std::max<int64_t>(16, round_up(ceil_div(w, 8), 4));
-            if (rp <= 32) rows = 2 * rp;
+            // The window count and the value reach 2w, beyond 8-bit lanes.
+            kbits = 15;
+            if (rows_for(8, 4, 16, 32)) rows *= 2;
         }
     }
-    const Variant *v = (rows > 0) ? find_variant(bits, rows, groups, score) : nullptr;
+    const Variant *v = (rows > 0) ? find_variant(kbits, rows, groups, score) : nullptr;
     if (!v) {
         if (why) {
             char buf[160];
@@ -77,20 +89,24 @@ bool choose_variant(int w, bool score, int want_groups, Plan *pl, std::string *w
     pl->score = score;
     pl->comb_rows = score ? 2 * w : w;
     pl->max_value = score ? 2 * w : w;
-    // Exit ring and key range.  8-bit keys: the ring has next_pow2(2w + 2)
-    // slots (at least 32, at most 128) and keys stay below the ring size, so
-    // the kernel's exit counting needs no branch; the new key cycles through
-    // [w, ring - 1].  16-bit keys: 15-bit key range, ring = next_pow2(w + 1).
-    if (bits == 8) {
+    // Exit ring and key range.  7-bit keys: the ring has next_pow2(2w + 2)
+    // slots (32..128) and keys stay below the ring size, so the kernel's exit
+    // counting needs no branch; the new key cycles through [w, ring - 1].
+    // Full 8-bit keys: ring 256, keys in [w, 255].  15-bit keys: ring =
+    // next_pow2(w + 1), keys below 32768.
+    if (v->key_bits == 7) {
         pl->ring = std::min(128, std::max(32, next_pow2(2 * w + 2)));
         pl->renorm = score ? (pl->ring - w) : (pl->ring - w) / 2;
+    } else if (v->key_bits == 8) {
+        pl->ring = 256;
+        pl->renorm = score ? (256 - w) : (256 - w) / 2;
     } else {
-        const int half = 1 << (bits - 1);
         pl->ring = next_pow2(w + 1);
-        pl->renorm = score ? (half - w) : (half - w) / 2;
+        pl->renorm = score ? (32768 - w) : (32768 - w) / 2;
     }
-    pl->strips_per_warp = (32 / groups) * (bits == 8 ? 4 : 2);
-    const int ngrp = 32 / groups;
+    const int nlanes = v->lane_bits == 8 ? 4 : 2;
+    pl->strips_per_warp = (32 / v->groups) * nlanes;
+    const int ngrp = 32 / v->groups;
     pl->smem = (size_t)kWarpsPerBlock * (size_t)(pl->ring * ngrp + kOB * (ngrp + 1)) * 4u;
     pl->warp_words = pl->ring * ngrp + kOB * (ngrp + 1);
     return true;

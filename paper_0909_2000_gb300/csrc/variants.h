@@ -12,6 +12,7 @@ typedef void (*comb_fn_t)(CombParams);
 typedef void (*batch_fn_t)(BatchParams);
 
 struct Variant {
+    int key_bits;    // 7 (8-bit lanes), 8 (8-bit lanes, full keys) or 15 (16-bit lanes)
     int lane_bits;   // 8 or 16
     int rows;        // R: physical comb rows per thread
     int groups;      // G: threads per strip group
@@ -26,6 +27,6 @@ const Variant *variant_table(int *count);
 }  // namespace ap
 
 // Instantiation helper: one template instance plus its registry entry.
-#define AP_VARIANT(LANES, BITS, R, G, SCORE, PADR)                                  \
-    { BITS, R, G, SCORE, &ap::comb_kernel<ap::LANES, R, G, SCORE, PADR>,                \
+#define AP_VARIANT(LANES, KEYBITS, BITS, R, G, SCORE, PADR)                         \
+    { KEYBITS, BITS, R, G, SCORE, &ap::comb_kernel<ap::LANES, R, G, SCORE, PADR>,       \
       &ap::comb_batch_kernel<ap::LANES, R, G, SCORE, PADR> }

@@ -60,15 +60,19 @@ def test_host_side_validation_without_gpu():
 
 
 @pytest.mark.parametrize("w,scores", [(1, ap.LCS), (16, ap.LCS), (100, ap.LCS), (120, ap.LCS),
-                                      (121, ap.LCS), (256, ap.LCS), (512, ap.LCS), (1, ap.SCORE),
+                                      (121, ap.LCS), (128, ap.LCS), (129, ap.LCS), (254, ap.LCS),
+                                      (255, ap.LCS), (256, ap.LCS), (512, ap.LCS), (1, ap.SCORE),
                                       (64, ap.SCORE), (65, ap.SCORE), (120, ap.SCORE),
-                                      (121, ap.SCORE), (256, ap.SCORE)])
+                                      (121, ap.SCORE), (254, ap.SCORE), (256, ap.SCORE)])
 def test_every_supported_window_has_a_variant(w, scores):
     pl = ap.plot_plan(w + 1000, w + 777, w, scores)
     rows = 2 * w if scores == ap.SCORE else w
     assert pl["comb_rows"] == rows
     assert pl["rows_per_lane"] * pl["lanes_per_strip"] >= rows
     assert pl["logical_cells"] == 1000 * 777 * w
+    # key width: 7-bit up to w = 120, then full 8-bit lanes up to 254 (LCS only,
+    # its values stay below 256), 16-bit lanes above
+    assert pl["lane_bits"] == (8 if (w <= 120 or (w <= 254 and scores == ap.LCS)) else 16)
     assert pl["physical_cells"] >= pl["logical_cells"] * (4 if scores == ap.SCORE else 1)
 
 

@@ -46,6 +46,9 @@ CASES = [
     (300, 500, 128, b"ACGT", (1, 0, 0)),
     (400, 700, 200, b"AC", (1, 0, 0)),
     (600, 600, 256, b"ACGT", (1, 0, 0)),
+    (500, 620, 254, b"AC", (1, 0, 0)),
+    (430, 700, 129, b"ACGT", (1, 0, 0)),
+    (380, 450, 173, bytes(range(256)), (1, 0, 0)),
     (40, 45, 3, b"AC", (2, 1, 0)),
     (190, 211, 16, b"ACDEFGHIKLMNPQRSTVWY", (2, 1, 0)),
     (300, 333, 64, b"ACDEFGHIKLMNPQRSTVWY", (2, 1, 0)),
@@ -55,6 +58,8 @@ CASES = [
     (400, 401, 120, b"ACGT", (2, 1, 0)),
     (420, 430, 121, b"ACGT", (2, 1, 0)),
     (600, 640, 200, b"AC", (2, 1, 0)),
+    (600, 620, 254, b"ACGT", (2, 1, 0)),
+    (620, 640, 255, b"ACGT", (2, 1, 0)),
 ]
 
 
@@ -74,7 +79,8 @@ def test_random_shapes(cuda_lib, m, n, w, alph, scores):
 
 
 @pytest.mark.parametrize("w,scores", [(9, (1, 0, 0)), (100, (1, 0, 0)), (150, (1, 0, 0)),
-                                      (20, (2, 1, 0)), (90, (2, 1, 0))])
+                                      (300, (1, 0, 0)), (20, (2, 1, 0)), (90, (2, 1, 0)),
+                                      (140, (2, 1, 0))])
 def test_tiny_chunks_cross_many_tiles(cuda_lib, w, scores):
     ap = cuda_lib
     x = synth.dna(5, 1, w + 140)
