@@ -55,8 +55,15 @@ typedef enum ap_status {
  *              where S is the (1, 0, -1/2) score.  Computed as the LCS of the
  *              '$'-interleaved windows (Section 2), with Definition 3.2's
  *              (w, 2) restriction.
- * Any scheme (a, b, g) with g < 0 maps to {a - 2g, b - 2g, 0} after scaling
- * to integers; other normalised pairs return AP_E_UNSUPPORTED.
+ *   {m, x, 0}  2 <= m <= 4, 1 <= x < m: the same construction for other small
+ *              rational scores (Section 2: "a constant factor blow-up of the
+ *              input strings"): every character becomes x copies of '$'
+ *              followed by m - x copies of itself, and P = the LCS of the
+ *              blown-up windows = the best alignment score, x w <= P <= m w.
+ *              Windows up to 32 (8-bit lanes) or 128 (16-bit lanes).
+ * A scheme (a, b, g) with g < 0 maps to {a - 2g, b - 2g, 0} after scaling to
+ * integers (and the plot value to S - 2wg).  Other normalised pairs, and
+ * {m, 0, 0} with m > 1 (m times the LCS), return AP_E_UNSUPPORTED.
  */
 typedef struct ap_scores {
     int32_t match;
@@ -141,7 +148,7 @@ ap_status ap_set_lanes_per_strip(int32_t groups);
  *
  * Errors: AP_E_INVAL for null pointers, w < 1, ld < cols, an element size
  * other than 1 or 2, or uint8 output when the largest possible value
- * (w for LCS, 2w for {2,1,0}) exceeds 255; AP_E_UNSUPPORTED for other
+ * (match * w) exceeds 255; AP_E_UNSUPPORTED for other
  * score schemes or w beyond the largest compiled comb height;
  * AP_E_CUDA if a launch fails.  If m <= w or n <= w the plot is empty:
  * nothing is written and AP_OK is returned.  Stream-ordered; allocates no

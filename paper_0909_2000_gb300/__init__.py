@@ -222,7 +222,7 @@ def alignment_plot(x, y, w: int, scores=LCS, out=None, out_dtype=None, stream=No
     sc = _scores(scores)
     if out is None:
         if out_dtype is None:
-            vmax = 2 * w if sc.match == 2 else w
+            vmax = max(1, sc.match) * w
             out_dtype = torch.uint8 if vmax <= 255 else torch.int16
         out = empty_plot(rows, cols, out_dtype, x.device)
     if out.element_size() not in (1, 2) or not out.is_cuda:

@@ -25,32 +25,40 @@ NVCC = os.environ.get("NVCC", "nvcc")
 
 def _variants():
     """(lane type, key bits, lane bits, rows per thread, threads per strip
-    group, score mode, padding rows) of every compiled comb kernel."""
+    group, nu, mu, padding units) of every compiled comb kernel.  (nu, mu) is
+    the score blow-up {nu, mu, 0}; (1, 0) is LCS."""
     v = []
     # LCS, 7-bit keys in 8-bit lanes, one thread per strip group: w <= 120
     for r in range(8, 121, 8):
-        v.append(("U8Lanes", 7, 8, r, 1, False, 8))
+        v.append(("U8Lanes", 7, 8, r, 1, 1, 0, 8))
     # LCS, 7-bit keys, a strip group's rows split over 2 or 4 threads
     for g, rs in ((2, range(16, 61, 4)), (4, range(8, 33, 4))):
         for r in rs:
-            v.append(("U8Lanes", 7, 8, r, g, False, 8))
-    # score mode, 7-bit pair keys: w <= 64 on one thread, w <= 120 on two
+            v.append(("U8Lanes", 7, 8, r, g, 1, 0, 8))
+    # {2,1,0}, 7-bit pair keys: w <= 64 on one thread, w <= 120 on two
     for rp in range(4, 65, 4):
-        v.append(("U8Lanes", 7, 8, 2 * rp, 1, True, 8))
+        v.append(("U8Lanes", 7, 8, 2 * rp, 1, 2, 1, 4))
     for rp in range(36, 61, 4):
-        v.append(("U8Lanes", 7, 8, 2 * rp, 2, True, 8))
+        v.append(("U8Lanes", 7, 8, 2 * rp, 2, 2, 1, 4))
     # LCS, full 8-bit keys in 8-bit lanes: 120 < w <= 254 on 2 or 4 threads
-    # (score mode keeps 16-bit lanes above w = 120: its values reach 2w)
-    v.append(("U8FLanes", 8, 8, 64, 2, False, 8))
+    # (blown-up scores keep 16-bit lanes above w = 120: their values reach nu w)
+    v.append(("U8FLanes", 8, 8, 64, 2, 1, 0, 8))
     for r in range(32, 65, 4):
-        v.append(("U8FLanes", 8, 8, r, 4, False, 8))
+        v.append(("U8FLanes", 8, 8, r, 4, 1, 0, 8))
     # LCS, 15-bit keys in 16-bit lanes, rows split over 2, 4 or 8 threads: w <= 512
     for g in (2, 4, 8):
         for r in range(16, 65, 8):
-            v.append(("U16Lanes", 15, 16, r, g, False, 8))
-    # score mode, 15-bit pair keys, 8 threads: w <= 256
+            v.append(("U16Lanes", 15, 16, r, g, 1, 0, 8))
+    # {2,1,0}, 15-bit pair keys, 8 threads: w <= 256
     for rp in range(16, 33, 4):
-        v.append(("U16Lanes", 15, 16, 2 * rp, 8, True, 8))
+        v.append(("U16Lanes", 15, 16, 2 * rp, 8, 2, 1, 4))
+    # other blow-ups {nu, mu, 0}, nu = 3, 4: w <= 32 on one thread (8-bit
+    # lanes), w <= 128 on 8 threads (16-bit lanes)
+    for nu, mu in ((3, 1), (3, 2), (4, 1), (4, 2), (4, 3)):
+        for rp in (8, 16, 24, 32):
+            v.append(("U8Lanes", 7, 8, nu * rp, 1, nu, mu, 8))
+        for rp in (4, 8, 12, 16):
+            v.append(("U16Lanes", 15, 16, nu * rp, 8, nu, mu, 4))
     return v
 
 
@@ -68,11 +76,11 @@ def _generate() -> list[str]:
                  "extern const Variant kVariants%d[];" % k,
                  "extern const int kNumVariants%d;" % k,
                  "const Variant kVariants%d[] = {" % k]
-        for (lanes, kbits, bits, r, g, score, padr) in part:
-            lines.append("    AP_VARIANT(%s, %d, %d, %d, %d, %s, %d)," % (
-                lanes, kbits, bits, r, g, "true" if score else "false", padr))
+        for (lanes, kbits, bits, r, g, nu, mu, padu) in part:
+            lines.append("    AP_VARIANT(%s, %d, %d, %d, %d, %d, %d, %d)," % (
+                lanes, kbits, bits, r, g, nu, mu, padu))
         if not part:
-            lines.append("    {0, 0, 0, 0, false, nullptr, nullptr},")
+            lines.append("    {0, 0, 0, 0, 0, 0, nullptr, nullptr},")
         lines += ["};", "const int kNumVariants%d = %d;" % (k, len(part)), "}  // namespace ap", ""]
         paths.append(_write_if_changed(os.path.join(gen, "variants_%02d.cu" % k), "\n".join(lines)))
     table = ['#include <vector>', '#include <mutex>', '#include "variants.h"', "namespace ap {"]

@@ -15,8 +15,8 @@ ap_status fail_cuda(cudaError_t e, const char *what);
 
 struct Plan;
 
-// Scores -> mode (false: LCS, true: {2,1,0}); errors for other schemes.
-ap_status score_mode(const ap_scores *sc, bool *score);
+// Scores -> blow-up {nu, mu, 0} (nu = 1: LCS); errors for other schemes.
+ap_status score_mode(const ap_scores *sc, int *nu, int *mu);
 
 // Validated plan of one plot: variant (groups > 0 requests threads per strip
 // group), tiling (chunk > 0 forces the chunk).

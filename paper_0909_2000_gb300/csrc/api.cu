@@ -31,17 +31,23 @@ ap_status fail_cuda(cudaError_t e, const char *what)
     return fail(AP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// Scores -> mode.  Normalised form: gap 0, 0 <= mismatch < match.
-ap_status score_mode(const ap_scores *sc, bool *score)
+// Scores -> blow-up {nu, mu, 0}.  Normalised form: gap 0, 0 <= mismatch < match.
+ap_status score_mode(const ap_scores *sc, int *nu, int *mu)
 {
-    if (!sc) { *score = false; return AP_OK; }
+    *nu = 1;
+    *mu = 0;
+    if (!sc) return AP_OK;
     if (sc->gap != 0 || sc->mismatch < 0 || sc->mismatch >= sc->match)
         return fail(AP_E_INVAL, "scores {%d,%d,%d} are not normalised (need gap 0, "
                     "0 <= mismatch < match)", sc->match, sc->mismatch, sc->gap);
-    if (sc->match == 1 && sc->mismatch == 0) { *score = false; return AP_OK; }
-    if (sc->match == 2 && sc->mismatch == 1) { *score = true; return AP_OK; }
-    return fail(AP_E_UNSUPPORTED, "scores {%d,%d,0}: only {1,0,0} and {2,1,0} are built",
-                sc->match, sc->mismatch);
+    if (sc->match == 1) return AP_OK;   // {1,0,0}: LCS
+    if (sc->match <= 4 && sc->mismatch >= 1) {
+        *nu = sc->match;
+        *mu = sc->mismatch;
+        return AP_OK;
+    }
+    return fail(AP_E_UNSUPPORTED, "scores {%d,%d,0}: built are {1,0,0} and {m,x,0} with "
+                "2 <= m <= 4, 1 <= x < m", sc->match, sc->mismatch);
 }
 
 int current_device()
@@ -59,11 +65,11 @@ ap_status plan_plot(int64_t m, int64_t n, int32_t w, const ap_scores *scores, in
 {
     if (w < 1) return fail(AP_E_INVAL, "w = %d: the window length must be >= 1", w);
     if (m < 0 || n < 0) return fail(AP_E_INVAL, "negative sequence length");
-    bool score = false;
-    ap_status s = score_mode(scores, &score);
+    int nu = 1, mu = 0;
+    ap_status s = score_mode(scores, &nu, &mu);
     if (s != AP_OK) return s;
     std::string why;
-    if (!choose_variant(w, score, groups, pl, &why))
+    if (!choose_variant(w, nu, mu, groups, pl, &why))
         return fail(AP_E_UNSUPPORTED, "%s", why.c_str());
     const int64_t rows = std::max<int64_t>(0, m - w), cols = std::max<int64_t>(0, n - w);
     tile_plan(pl, rows, cols, chunk, current_device());

@@ -38,9 +38,9 @@ struct Group {
     cudaEvent_t done = nullptr;
 };
 
-// Process-wide cache of tuned schedules: (score, w, SMs) -> (groups, chunk).
+// Process-wide cache of tuned schedules: (nu, mu, w, SMs) -> (groups, chunk).
 std::mutex g_tune_mu;
-std::map<std::tuple<bool, int, int>, std::pair<int, int64_t>> g_tuned;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int64_t>> g_tuned;
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -61,7 +61,7 @@ std::vector<BatchTile> make_tiles(const std::vector<Plan> &plans, const std::vec
         for (int64_t ch = 0; ch < pl.nchunks; ++ch) {
             const int64_t cols = std::min(pl.chunk, pl.cols - ch * pl.chunk);
             const int64_t units = cols + pl.w - 1;
-            const int64_t cost = units * (int64_t)pl.v->rows * (pl.score ? 2 : 1);
+            const int64_t cost = units * (int64_t)pl.v->rows * pl.nu;
             for (int64_t sg = 0; sg < pl.nsg; ++sg)
                 all.push_back({cost, BatchTile{j, (int32_t)sg, (int32_t)ch, 0}});
         }
@@ -177,11 +177,11 @@ cudaError_t upload_params(ap_batch *b)
 
 // Autotune one window class: try (threads per strip, chunk) candidates on the
 // class's jobs, timing one persistent launch each; returns the fastest.
-ap_status tune_class(ap_batch *b, const std::vector<int> &idx, bool score, int w,
+ap_status tune_class(ap_batch *b, const std::vector<int> &idx, int nu, int w,
                      std::pair<int, int64_t> *best, double *tune_ms)
 {
     std::vector<int> groups_c = {0};
-    if (!score && w <= 120) groups_c = {1, 2};
+    if (nu == 1 && w <= 120) groups_c = {1, 2};
     std::vector<int64_t> chunks_c = {1024, 4096, 16384};
     float best_ms = 1e30f;
     *best = {0, default_chunk(w)};
@@ -280,13 +280,14 @@ ap_status ap_batch_create(const ap_job *jobs, int32_t njobs, const ap_batch_opti
 
     // Autotune each window class (score mode, w), unless fixed by options.
     if (opt.autotune && opt.chunk == 0 && opt.lanes_per_strip == 0) {
-        std::map<std::pair<bool, int>, std::vector<int>> classes;
+        std::map<std::tuple<int, int, int>, std::vector<int>> classes;
         for (size_t j = 0; j < b->jobs.size(); ++j)
-            classes[{b->plans[j].score, b->plans[j].w}].push_back((int)j);
+            classes[std::make_tuple(b->plans[j].nu, b->plans[j].mu, b->plans[j].w)].push_back((int)j);
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, std::max(0, b->device));
         for (auto &kv : classes) {
-            const auto key = std::make_tuple(kv.first.first, kv.first.second, sms);
+            const auto key = std::make_tuple(std::get<0>(kv.first), std::get<1>(kv.first),
+                                             std::get<2>(kv.first), sms);
             std::pair<int, int64_t> best;
             bool cached = false;
             {
@@ -298,8 +299,8 @@ ap_status ap_batch_create(const ap_job *jobs, int32_t njobs, const ap_batch_opti
                 }
             }
             if (!cached) {
-                ap_status s = tune_class(b, kv.second, kv.first.first, kv.first.second, &best,
-                                         &b->info.tune_ms);
+                ap_status s = tune_class(b, kv.second, std::get<0>(kv.first),
+                                         std::get<2>(kv.first), &best, &b->info.tune_ms);
                 if (s != AP_OK) {
                     release(b);
                     return s;

@@ -339,8 +339,11 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
 // L      lane format (U8Lanes / U16Lanes)
 // R      physical comb rows held by each thread
 // G      threads per strip group (the strip's rows are split over them)
-// SCORE  false: LCS; true: '$'-interleaved strings ({2,1,0} scores)
-// PADR   trailing rows of each thread that may be padding (never match)
+// NU, MU blow-up of the score scheme {NU, MU, 0}: every character becomes
+//        MU '$' followed by NU - MU copies of itself (Section 2 for {2,1,0});
+//        NU = 1 is LCS
+// PADU   trailing units (rows for LCS, row groups of NU otherwise) of each
+//        thread that may be padding (never match)
 //
 // Each step combs two physical columns, interleaved row by row, so a thread
 // always has two independent dependency chains:
@@ -348,17 +351,18 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
 //   score: the '$' column and the character column of y' pair u (keys per pair).
 // Threads of a strip group are skewed by one step: thread g works on unit
 // u = s - g and takes its top seaweeds from thread g-1 by warp shuffle.
-template <class L, int R, int G, bool SCORE, int PADR>
+template <class L, int R, int G, int NU, int MU, int PADU>
 __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64_t ch,
                                           uint32_t *ring)
 {
+    constexpr bool SCORE = NU > 1;
     constexpr int NS = L::NS;
     constexpr int NGRP = 32 / G;
     constexpr int SPW = NGRP * NS;                    // strips per warp
-    constexpr int RP = SCORE ? R / 2 : R;             // x rows per thread
+    constexpr int RP = R / NU;                        // x characters (units) per thread
     constexpr int NQ = RP / L::RPW + 1;               // aligned x words
-    constexpr int PADU = SCORE ? PADR / 2 : PADR;     // padding units (rows or pairs)
-    static_assert(R % (SCORE ? 2 * L::RPW : L::RPW) == 0, "R must fill whole x words");
+    static_assert(NU >= 1 && MU >= 0 && MU < NU && (NU > 1 || MU == 0), "bad blow-up");
+    static_assert(R % (NU * L::RPW) == 0, "R must fill whole x words");
     static_assert(PADU <= RP, "padding window larger than the lane");
 
     const int lane = threadIdx.x & 31;
@@ -411,7 +415,7 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
     const int ncomb = (int)(c1 - c0) + wk - 1;
     const int nunits = SCORE ? ncomb : (ncomb + 1) / 2;
     const int steps = nunits + G - 1;
-    const uint32_t wvec = (uint32_t)(SCORE ? 2 * wk : wk) * L::ONES;
+    const uint32_t wvec = (uint32_t)(NU * wk) * L::ONES;
     const uint32_t inval_bias = (uint32_t)((1u << (L::BITS - 1)) - (uint32_t)wk) * L::ONES;
     const int kdrop = SCORE ? p.renorm : 2 * p.renorm;
     const uint32_t rr_bias = (uint32_t)((1u << (L::BITS - 1)) - (uint32_t)kdrop) * L::ONES;
@@ -434,7 +438,9 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
     int kc = wk;        // key of the first seaweed starting in this thread's unit
     int since = 0;      // steps since the last renormalisation
     uint32_t d = 0;     // per strip: seaweeds counted in the current window
-    uint32_t vdown0 = 0, vdown1 = 0;
+    uint32_t vdown[NU > 1 ? NU : 2];
+#pragma unroll
+    for (int c = 0; c < (NU > 1 ? NU : 2); ++c) vdown[c] = 0u;
 
     // Exit counting (Theorem 3.1's queue B as a ring of "left validly" flags,
     // one byte per strip, indexed by start column (LCS) or pair (score)).
@@ -522,18 +528,17 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
         const uint32_t knew0 = (uint32_t)kc * L::ONES;
         const uint32_t knew1 = SCORE ? knew0 : knew0 + L::ONES;
 
-        uint32_t va, vb;                  // top seaweeds of the two columns
-        if (G > 1) {
-            const uint32_t in0 = __shfl_up_sync(0xffffffffu, vdown0, 1);
-            const uint32_t in1 = __shfl_up_sync(0xffffffffu, vdown1, 1);
-            va = (g == 0) ? knew0 : in0;
-            vb = (g == 0) ? knew1 : in1;
-        } else {
-            va = knew0;
-            vb = knew1;
-        }
-
         if (!SCORE) {
+            uint32_t va, vb;              // top seaweeds of the two columns
+            if (G > 1) {
+                const uint32_t in0 = __shfl_up_sync(0xffffffffu, vdown[0], 1);
+                const uint32_t in1 = __shfl_up_sync(0xffffffffu, vdown[1], 1);
+                va = (g == 0) ? knew0 : in0;
+                vb = (g == 0) ? knew1 : in1;
+            } else {
+                va = knew0;
+                vb = knew1;
+            }
             const uint32_t yb0 = ychar(2 * u) * L::ONES;
             const uint32_t yb1 = ychar(2 * u + 1) * L::ONES;
             uint32_t mm0[NQ], mm1[NQ];
@@ -555,7 +560,23 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
                 cell<L>(h[k], va, m0, neg1);
                 cell<L>(h[k], vb, m1, neg1);
             }
+            vdown[0] = va;
+            vdown[1] = vb;
         } else {
+            // One unit of y': MU '$' columns, then NU - MU columns of y[u].  Rows
+            // come in units of NU: MU '$' rows, then NU - MU rows of the x
+            // character.  '$' meets '$': match (unless padding); '$' meets a
+            // character: mismatch; character meets character: compare.
+            uint32_t v[NU];
+#pragma unroll
+            for (int c = 0; c < NU; ++c) {
+                if (G > 1) {
+                    const uint32_t in = __shfl_up_sync(0xffffffffu, vdown[c], 1);
+                    v[c] = (g == 0) ? knew0 : in;
+                } else {
+                    v[c] = knew0;
+                }
+            }
             const uint32_t yb = ychar(u) * L::ONES;
             uint32_t mm[NQ];
 #pragma unroll
@@ -564,25 +585,34 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
             for (int q = 0; q < RP; ++q) {
                 const int pi = q - (RP - PADU);
                 const uint32_t pad = (pi >= 0) ? padm[pi < 0 ? 0 : pi] : 0u;
-                // '$' column: '$' row matches (unless padding), x row mismatches.
-                if (pi >= 0) {
-                    cell<L>(h[2 * q], va, pad, neg1);
-                } else {
-                    const uint32_t tmp = h[2 * q];
-                    h[2 * q] = va;
-                    va = tmp;
-                }
-                cell_mismatch<L>(h[2 * q + 1], va, neg1);
-                // character column: '$' row mismatches, x row compares.
-                cell_mismatch<L>(h[2 * q], vb, neg1);
                 const int qq = q / L::RPW, r = q % L::RPW;
                 uint32_t mq = (r == 0) ? mm[qq] : row_shift(mm[qq], mm[qq + 1], shm(r));
                 if (pi >= 0) mq |= pad;
-                cell<L>(h[2 * q + 1], vb, mq, neg1);
+#pragma unroll
+                for (int rho = 0; rho < NU; ++rho) {
+                    const int k = NU * q + rho;
+#pragma unroll
+                    for (int c = 0; c < NU; ++c) {
+                        const bool row_dollar = rho < MU, col_dollar = c < MU;
+                        if (row_dollar && col_dollar) {
+                            if (pi >= 0) {
+                                cell<L>(h[k], v[c], pad, neg1);
+                            } else {
+                                const uint32_t tmp = h[k];
+                                h[k] = v[c];
+                                v[c] = tmp;
+                            }
+                        } else if (row_dollar != col_dollar) {
+                            cell_mismatch<L>(h[k], v[c], neg1);
+                        } else {
+                            cell<L>(h[k], v[c], mq, neg1);
+                        }
+                    }
+                }
             }
+#pragma unroll
+            for (int c = 0; c < NU; ++c) vdown[c] = v[c];
         }
-        vdown0 = va;
-        vdown1 = vb;
 
         // ---- bottom threads: count exits (Theorem 3.1) and stage the plot ----
         const int ubot = s - (G - 1);       // the bottom threads' unit (warp-uniform)
@@ -591,21 +621,21 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
             const int col0 = 2 * ubot, col1 = 2 * ubot + 1;
             if (bottom) {
                 expire(col0);
-                count_exit(va, knew0, col0);
+                count_exit(vdown[0], knew0, col0);
                 stage_out(col0);
             }
             if (ubot >= 0) maybe_flush(col0);
             if (bottom && col1 < ncomb) {
                 expire(col1);
-                count_exit(vb, knew1, col1);
+                count_exit(vdown[1], knew1, col1);
                 stage_out(col1);
             }
             if (ubot >= 0) maybe_flush(col1);
         } else {
             if (bottom) {
                 expire(ubot);
-                count_exit(va, knew0, ubot);
-                count_exit(vb, knew0, ubot);
+#pragma unroll
+                for (int c = 0; c < NU; ++c) count_exit(vdown[c], knew0, ubot);
                 stage_out(ubot);
             }
             if (ubot >= 0) maybe_flush(ubot);
@@ -622,7 +652,7 @@ __host__ __device__ constexpr int comb_warp_words(int ring)
 }
 
 // Plain launch: one warp per tile; tiles are numbered strip group fastest.
-template <class L, int R, int G, bool SCORE, int PADR>
+template <class L, int R, int G, int NU, int MU, int PADU>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, AP_MIN_BLOCKS)
 comb_kernel(CombParams p)
 {
@@ -630,7 +660,7 @@ comb_kernel(CombParams p)
     const int wid = threadIdx.x >> 5;
     const int64_t tile = p.tile0 + (int64_t)blockIdx.x * kWarpsPerBlock + wid;
     if (tile >= p.ntiles) return;
-    comb_tile<L, R, G, SCORE, PADR>(p, tile % p.nsg, tile / p.nsg,
+    comb_tile<L, R, G, NU, MU, PADU>(p, tile % p.nsg, tile / p.nsg,
                                     smem + wid * comb_warp_words<G>(p.ring));
 }
 
@@ -653,7 +683,7 @@ struct BatchParams {
 // Persistent launch over a batch: every warp takes the next tile of the work
 // list until it is exhausted.  Each tile is combed exactly as a plain launch
 // combs it, so results are bit-identical to one call per job.
-template <class L, int R, int G, bool SCORE, int PADR>
+template <class L, int R, int G, int NU, int MU, int PADU>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, AP_MIN_BLOCKS)
 comb_batch_kernel(BatchParams b)
 {
@@ -667,7 +697,7 @@ comb_batch_kernel(BatchParams b)
         t = __shfl_sync(0xffffffffu, t, 0);
         if ((int64_t)t >= b.ntiles) break;
         const BatchTile bt = b.tiles[t];
-        comb_tile<L, R, G, SCORE, PADR>(b.jobs[bt.job], bt.sg, bt.ch, wsm);
+        comb_tile<L, R, G, NU, MU, PADU>(b.jobs[bt.job], bt.sg, bt.ch, wsm);
         __syncwarp();
     }
 }

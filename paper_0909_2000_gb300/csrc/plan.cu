@@ -14,13 +14,13 @@ namespace {
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
-const Variant *find_variant(int key_bits, int rows, int groups, bool score)
+const Variant *find_variant(int key_bits, int rows, int groups, int nu, int mu)
 {
     int count = 0;
     const Variant *t = variant_table(&count);
     for (int i = 0; i < count; ++i)
         if (t[i].key_bits == key_bits && t[i].rows == rows && t[i].groups == groups &&
-            t[i].score == score)
+            t[i].nu == nu && t[i].mu == mu)
             return &t[i];
     return nullptr;
 }
@@ -34,8 +34,9 @@ int next_pow2(int v)
 
 }  // namespace
 
-bool choose_variant(int w, bool score, int want_groups, Plan *pl, std::string *why)
+bool choose_variant(int w, int nu, int mu, int want_groups, Plan *pl, std::string *why)
 {
+    const bool score = nu > 1;
     // key_bits: 7 (w <= 120), 8 (LCS, w <= 254: values fit a byte), else 15.
     int kbits = 0, rows = 0, groups = 0;
     auto rows_for = [&](int g, int unit, int lo, int hi) -> bool {
@@ -61,7 +62,7 @@ bool choose_variant(int w, bool score, int want_groups, Plan *pl, std::string *w
             for (int g : {2, 4, 8})
                 if (rows_for(g, 8, 16, 64)) break;
         }
-    } else {
+    } else if (nu == 2 && mu == 1) {
         if (w <= 64) {
             kbits = 7;
             if (rows_for(1, 4, 4, 64)) rows *= 2;
@@ -73,22 +74,33 @@ bool choose_variant(int w, bool score, int want_groups, Plan *pl, std::string *w
             kbits = 15;
             if (rows_for(8, 4, 16, 32)) rows *= 2;
         }
+    } else {
+        // {3 or 4, mu, 0}: 8-bit lanes while nu * w stays below 256 (w <= 32),
+        // then 16-bit lanes on 8 threads.
+        if (w <= 32) {
+            kbits = 7;
+            if (rows_for(1, 8, 8, 32)) rows *= nu;
+        } else {
+            kbits = 15;
+            if (rows_for(8, 4, 4, 16)) rows *= nu;
+        }
     }
-    const Variant *v = (rows > 0) ? find_variant(kbits, rows, groups, score) : nullptr;
+    const Variant *v = (rows > 0) ? find_variant(kbits, rows, groups, nu, mu) : nullptr;
     if (!v) {
         if (why) {
             char buf[160];
-            snprintf(buf, sizeof buf, "no compiled comb variant for w=%d (%s mode)", w,
-                     score ? "score" : "LCS");
+            snprintf(buf, sizeof buf, "no compiled comb variant for w=%d with scores {%d,%d,0}",
+                     w, nu, mu);
             *why = buf;
         }
         return false;
     }
     pl->v = v;
     pl->w = w;
-    pl->score = score;
-    pl->comb_rows = score ? 2 * w : w;
-    pl->max_value = score ? 2 * w : w;
+    pl->nu = nu;
+    pl->mu = mu;
+    pl->comb_rows = nu * w;
+    pl->max_value = nu * w;
     // Exit ring and key range.  7-bit keys: the ring has next_pow2(2w + 2)
     // slots (32..128) and keys stay below the ring size, so the kernel's exit
     // counting needs no branch; the new key cycles through [w, ring - 1].
@@ -147,7 +159,7 @@ int64_t physical_cells(const Plan &pl)
 {
     // every tile combs (its plot columns + w - 1) units of R rows x strips per warp
     const int64_t units = pl.cols + pl.nchunks * (int64_t)(pl.w - 1);
-    const int64_t cols_phys = pl.score ? 2 * units : units;
+    const int64_t cols_phys = (int64_t)pl.nu * units;
     const int64_t comb_rows_padded = (int64_t)pl.v->rows * pl.v->groups;
     return pl.nsg * (int64_t)pl.strips_per_warp * cols_phys * comb_rows_padded;
 }

@@ -11,8 +11,8 @@ namespace ap {
 struct Plan {
     const Variant *v = nullptr;
     int w = 0;            // window length (key window)
-    bool score = false;   // '$'-interleaved ({2,1,0}) mode
-    int comb_rows = 0;    // physical comb height: w or 2w
+    int nu = 1, mu = 0;   // score blow-up {nu, mu, 0}; nu = 1 is LCS
+    int comb_rows = 0;    // physical comb height: nu * w
     int renorm = 0;       // steps between key renormalisations
     int ring = 0;         // exit-ring slots (power of two > w)
     int strips_per_warp = 0;
@@ -20,13 +20,13 @@ struct Plan {
     int64_t chunk = 0, nchunks = 0, nsg = 0, ntiles = 0;
     size_t smem = 0;      // dynamic shared memory per block
     int warp_words = 0;   // shared-memory words per warp
-    int max_value = 0;    // largest plot value: w or 2w
+    int max_value = 0;    // largest plot value: nu * w
 };
 
-// Picks the variant for (w, score).  `groups` > 0 asks for that many
-// threads per strip group (when a variant exists).  Returns false (with a
-// message) when no compiled variant covers the request.
-bool choose_variant(int w, bool score, int groups, Plan *pl, std::string *why);
+// Picks the variant for window w and score blow-up {nu, mu, 0}.  `groups` > 0
+// asks for that many threads per strip group (when a variant exists).
+// Returns false (with a message) when no compiled variant covers the request.
+bool choose_variant(int w, int nu, int mu, int groups, Plan *pl, std::string *why);
 
 // Tiles a rows x cols plot for the chosen variant.  `chunk_hint` > 0 forces
 // the column chunk (rounded up to a multiple of 32).

@@ -16,7 +16,7 @@ struct Variant {
     int lane_bits;   // 8 or 16
     int rows;        // R: physical comb rows per thread
     int groups;      // G: threads per strip group
-    bool score;      // '$'-interleaved strings
+    int nu, mu;      // score blow-up {nu, mu, 0}; nu = 1 is LCS
     comb_fn_t fn;
     batch_fn_t batch_fn;
 };
@@ -27,6 +27,6 @@ const Variant *variant_table(int *count);
 }  // namespace ap
 
 // Instantiation helper: one template instance plus its registry entry.
-#define AP_VARIANT(LANES, KEYBITS, BITS, R, G, SCORE, PADR)                         \
-    { KEYBITS, BITS, R, G, SCORE, &ap::comb_kernel<ap::LANES, R, G, SCORE, PADR>,       \
-      &ap::comb_batch_kernel<ap::LANES, R, G, SCORE, PADR> }
+#define AP_VARIANT(LANES, KEYBITS, BITS, R, G, NU, MU, PADU)                        \
+    { KEYBITS, BITS, R, G, NU, MU, &ap::comb_kernel<ap::LANES, R, G, NU, MU, PADU>,     \
+      &ap::comb_batch_kernel<ap::LANES, R, G, NU, MU, PADU> }

@@ -44,7 +44,13 @@ def test_host_side_validation_without_gpu():
         ap.plot_shape(10, 10, 0)
     assert e.value.status == ap.AP_E_INVAL
     with pytest.raises(ap.ApError) as e:
-        ap.plot_plan(100, 100, 10, (3, 1, 0))
+        ap.plot_plan(100, 100, 10, (5, 1, 0))
+    assert e.value.status == ap.AP_E_UNSUPPORTED
+    with pytest.raises(ap.ApError) as e:
+        ap.plot_plan(100, 100, 10, (2, 0, 0))      # 2 x LCS: not built
+    assert e.value.status == ap.AP_E_UNSUPPORTED
+    with pytest.raises(ap.ApError) as e:
+        ap.plot_plan(1000, 1000, 129, (3, 1, 0))   # beyond the compiled windows
     assert e.value.status == ap.AP_E_UNSUPPORTED
     with pytest.raises(ap.ApError) as e:
         ap.plot_plan(100, 100, 10, (1, 1, 0))     # not normalised
@@ -74,6 +80,15 @@ def test_every_supported_window_has_a_variant(w, scores):
     # its values stay below 256), 16-bit lanes above
     assert pl["lane_bits"] == (8 if (w <= 120 or (w <= 254 and scores == ap.LCS)) else 16)
     assert pl["physical_cells"] >= pl["logical_cells"] * (4 if scores == ap.SCORE else 1)
+
+
+@pytest.mark.parametrize("nu,mu", [(3, 1), (3, 2), (4, 1), (4, 2), (4, 3)])
+@pytest.mark.parametrize("w", [1, 7, 32, 33, 64, 128])
+def test_blown_up_score_schemes_have_variants(nu, mu, w):
+    pl = ap.plot_plan(w + 500, w + 300, w, (nu, mu, 0))
+    assert pl["comb_rows"] == nu * w
+    assert pl["rows_per_lane"] * pl["lanes_per_strip"] >= nu * w
+    assert pl["physical_cells"] >= pl["logical_cells"] * nu * nu
 
 
 def test_plan_of_the_100k_plot():

@@ -78,6 +78,24 @@ def test_random_shapes(cuda_lib, m, n, w, alph, scores):
         bad[:4].tolist(), g[tuple(bad[:4].T)].tolist(), o[tuple(bad[:4].T)].tolist())
 
 
+BLOWUP_CASES = [
+    (120, 130, 5, (3, 1, 0)), (200, 170, 17, (3, 2, 0)), (300, 260, 32, (4, 1, 0)),
+    (150, 222, 24, (4, 2, 0)), (190, 140, 9, (4, 3, 0)), (260, 300, 33, (3, 1, 0)),
+    (300, 330, 70, (4, 3, 0)), (420, 400, 128, (3, 2, 0)), (350, 300, 100, (4, 1, 0)),
+]
+
+
+@pytest.mark.parametrize("m,n,w,scores", BLOWUP_CASES)
+def test_blown_up_score_schemes(cuda_lib, m, n, w, scores):
+    ap = cuda_lib
+    seed = m + 3 * n + w + 7 * scores[0] + scores[1]
+    x = synth.protein(seed, 1, m)
+    y, _ = synth.plant(x, synth.protein(seed, 2, n), 1, min(m, n) // 3, seed, 5, synth.PROTEIN, 0.1, 0.05)
+    o = oracle.plot(x, y, w, scores[0], scores[1])
+    g = gpu_plot(ap, x, y, w, scores, torch.int16)
+    assert g.shape == o.shape and np.array_equal(g, o), np.argwhere(g != o)[:4].tolist()
+
+
 @pytest.mark.parametrize("w,scores", [(9, (1, 0, 0)), (100, (1, 0, 0)), (150, (1, 0, 0)),
                                       (300, (1, 0, 0)), (20, (2, 1, 0)), (90, (2, 1, 0)),
                                       (140, (2, 1, 0))])

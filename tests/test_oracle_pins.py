@@ -94,3 +94,25 @@ def test_checksum_bands_add_up():
     total = oracle.checksum(p)
     parts = (oracle.checksum(p[:20], 0) + oracle.checksum(p[20:], 20)) % (1 << 64)
     assert total == parts
+
+
+@pytest.mark.parametrize("nu,mu", [(2, 1), (3, 1), (3, 2), (4, 1), (4, 2), (4, 3)])
+def test_blow_up_reduction_small_rational_scores(nu, mu):
+    """Section 2: small rational scores reduce to LCS by blowing the strings
+    up.  Reading: every character becomes mu '$' then nu - mu copies of
+    itself.  Checked here by brute force (subsequence enumeration on the
+    blown-up windows against alignment enumeration with scores nu, mu, 0),
+    then the oracle's weighted recurrence against both."""
+    def blow(s):
+        out = bytearray()
+        for c in s:
+            out += bytes([0x24]) * mu + bytes([c]) * (nu - mu)
+        return bytes(out)
+    for t in range(12):
+        a = synth.alphabet_string(t, 1 + 10 * nu + mu, 1 + t % 3, np.frombuffer(b"ACG", np.uint8)).tobytes()
+        b = synth.alphabet_string(t, 2 + 10 * nu + mu, 1 + (t * 5) % 3, np.frombuffer(b"ACG", np.uint8)).tobytes()
+        brute_align = pins.alignment_bruteforce(a, b, nu, mu)
+        if len(a) * nu <= 9:
+            assert pins.lcs_bruteforce(blow(a), blow(b)) == brute_align
+        assert oracle.pair_score(a, b, nu, mu) == brute_align
+        assert oracle.pair_score(blow(a), blow(b), 1, 0) == brute_align
