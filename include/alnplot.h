@@ -160,6 +160,21 @@ ap_status ap_alignment_plot(const uint8_t *x, int64_t m, const uint8_t *y,
                             void *stream);
 
 /*
+ * Alignment plot with a vertical step (Section 3: "introducing a step size
+ * h, and only comparing w-windows starting at positions that are multiples
+ * of h"; Section 4 uses h = 5): plot row r holds the x-window starting at
+ * r * step, for 0 <= r < ceil((m - w) / step), against every y-window:
+ *     out[r*ld + j] = P[r * step][j]
+ * step = 1 is ap_alignment_plot.  With step > 1 this build covers LCS and
+ * {2,1,0} for w <= 120 (AP_E_UNSUPPORTED otherwise).  Other arguments and
+ * errors as in ap_alignment_plot; AP_E_INVAL for step < 1.
+ */
+ap_status ap_alignment_plot_step(const uint8_t *x, int64_t m, const uint8_t *y,
+                                 int64_t n, int32_t w, const ap_scores *scores,
+                                 int64_t step, void *out, int32_t out_elem_bytes,
+                                 int64_t ld, void *stream);
+
+/*
  * Bytes of device workspace ap_alignment_dots needs for these sizes.
  * bytes: host pointer, written on success.
  */

@@ -19,7 +19,7 @@ import threading
 
 __all__ = [
     "load", "ApError", "LCS", "SCORE", "plot_shape", "plot_plan", "alignment_plot",
-    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "set_chunk", "set_lanes_per_strip", "Batch", "Server", "DOT_DTYPE_FIELDS",
+    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "alignment_plot_step", "set_chunk", "set_lanes_per_strip", "Batch", "Server", "DOT_DTYPE_FIELDS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -100,6 +100,7 @@ def _declare(lib):
         "ap_plot_shape": [i64, i64, i32, i64p, i64p],
         "ap_plot_plan": [i64, i64, i32, sc, ctypes.POINTER(ap_plan)],
         "ap_alignment_plot": [p, i64, p, i64, i32, sc, p, i32, i64, p],
+        "ap_alignment_plot_step": [p, i64, p, i64, i32, sc, i64, p, i32, i64, p],
         "ap_dots_workspace_size": [i64, i64, i32, sc, i64p],
         "ap_alignment_dots": [p, i64, p, i64, i32, sc, i32, p, i64, i64p, p, i64, p],
         "ap_plot_dots_workspace_size": [i64, i64p],
@@ -234,6 +235,30 @@ def alignment_plot(x, y, w: int, scores=LCS, out=None, out_dtype=None, stream=No
                                     ctypes.c_void_p(y.data_ptr()), y.numel(), w,
                                     ctypes.byref(sc), ctypes.c_void_p(out.data_ptr()),
                                     out.element_size(), ld, _stream_handle(stream)))
+    return out
+
+
+def alignment_plot_step(x, y, w: int, step: int, scores=LCS, out=None, out_dtype=None,
+                        stream=None):
+    """Plot of every ``step``-th x-window: row r is x-window r * step against
+    every y-window (Section 3's vertical step h)."""
+    import torch
+    x, y = _dev_u8(x, "x"), _dev_u8(y, "y")
+    m, n = x.numel(), y.numel()
+    rows = -(-(m - w) // step) if m > w else 0
+    cols = max(0, n - w)
+    sc = _scores(scores)
+    if out is None:
+        if out_dtype is None:
+            out_dtype = torch.uint8 if max(1, sc.match) * w <= 255 else torch.int16
+        out = empty_plot(rows, cols, out_dtype, x.device)
+    if out.dim() != 2 or out.stride(1) != 1 or out.shape[0] < rows or out.shape[1] < cols:
+        raise ValueError("out must be a row-major 2-D tensor of at least %d x %d" % (rows, cols))
+    ld = out.stride(0) if rows > 1 else max(cols, out.shape[1])
+    _check(load().ap_alignment_plot_step(ctypes.c_void_p(x.data_ptr()), m, ctypes.c_void_p(y.data_ptr()),
+                                         n, w, ctypes.byref(sc), int(step),
+                                         ctypes.c_void_p(out.data_ptr()), out.element_size(), ld,
+                                         _stream_handle(stream)))
     return out
 
 

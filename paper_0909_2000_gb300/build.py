@@ -25,8 +25,8 @@ NVCC = os.environ.get("NVCC", "nvcc")
 
 def _variants():
     """(lane type, key bits, lane bits, rows per thread, threads per strip
-    group, nu, mu, padding units) of every compiled comb kernel.  (nu, mu) is
-    the score blow-up {nu, mu, 0}; (1, 0) is LCS."""
+    group, nu, mu, padding units, vertical-step layout) of every compiled comb
+    kernel.  (nu, mu) is the score blow-up {nu, mu, 0}; (1, 0) is LCS."""
     v = []
     # LCS, 7-bit keys in 8-bit lanes, one thread per strip group: w <= 120
     for r in range(8, 121, 8):
@@ -59,6 +59,14 @@ def _variants():
             v.append(("U8Lanes", 7, 8, nu * rp, 1, nu, mu, 8))
         for rp in (4, 8, 12, 16):
             v.append(("U16Lanes", 15, 16, nu * rp, 8, nu, mu, 4))
+    v = [t + (False,) for t in v]
+    # vertical step h > 1 (one x word per unit): LCS w <= 120 and {2,1,0} w <= 120
+    for r in range(8, 65, 8):
+        v.append(("U8Lanes", 7, 8, r, 1, 1, 0, 8, True))
+    for r in range(36, 61, 4):
+        v.append(("U8Lanes", 7, 8, r, 2, 1, 0, 8, True))
+    for rp in range(4, 33, 4):
+        v.append(("U8Lanes", 7, 8, 2 * rp, 4, 2, 1, 4, True))
     return v
 
 
@@ -76,11 +84,11 @@ def _generate() -> list[str]:
                  "extern const Variant kVariants%d[];" % k,
                  "extern const int kNumVariants%d;" % k,
                  "const Variant kVariants%d[] = {" % k]
-        for (lanes, kbits, bits, r, g, nu, mu, padu) in part:
-            lines.append("    AP_VARIANT(%s, %d, %d, %d, %d, %d, %d, %d)," % (
-                lanes, kbits, bits, r, g, nu, mu, padu))
+        for (lanes, kbits, bits, r, g, nu, mu, padu, xr) in part:
+            lines.append("    AP_VARIANT(%s, %d, %d, %d, %d, %d, %d, %d, %s)," % (
+                lanes, kbits, bits, r, g, nu, mu, padu, "true" if xr else "false"))
         if not part:
-            lines.append("    {0, 0, 0, 0, 0, 0, nullptr, nullptr},")
+            lines.append("    {0, 0, 0, 0, 0, 0, 0, nullptr, nullptr},")
         lines += ["};", "const int kNumVariants%d = %d;" % (k, len(part)), "}  // namespace ap", ""]
         paths.append(_write_if_changed(os.path.join(gen, "variants_%02d.cu" % k), "\n".join(lines)))
     table = ['#include <vector>', '#include <mutex>', '#include "variants.h"', "namespace ap {"]

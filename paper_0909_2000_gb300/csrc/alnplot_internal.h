@@ -19,9 +19,10 @@ struct Plan;
 ap_status score_mode(const ap_scores *sc, int *nu, int *mu);
 
 // Validated plan of one plot: variant (groups > 0 requests threads per strip
-// group), tiling (chunk > 0 forces the chunk).
+// group), tiling (chunk > 0 forces the chunk), vertical step (plot row r is the
+// x-window at r * step).
 ap_status plan_plot(int64_t m, int64_t n, int32_t w, const ap_scores *scores, int groups,
-                    int64_t chunk, Plan *pl);
+                    int64_t chunk, Plan *pl, int64_t step = 1);
 
 // Output-argument checks shared by the plain and batched calls.
 ap_status check_output(const Plan &pl, const void *x, const void *y, const void *out,

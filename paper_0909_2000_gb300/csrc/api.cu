@@ -61,17 +61,20 @@ int current_device()
 }
 
 ap_status plan_plot(int64_t m, int64_t n, int32_t w, const ap_scores *scores, int groups,
-                    int64_t chunk, Plan *pl)
+                    int64_t chunk, Plan *pl, int64_t step)
 {
+    if (step < 1) return fail(AP_E_INVAL, "step = %lld: must be >= 1", (long long)step);
     if (w < 1) return fail(AP_E_INVAL, "w = %d: the window length must be >= 1", w);
     if (m < 0 || n < 0) return fail(AP_E_INVAL, "negative sequence length");
     int nu = 1, mu = 0;
     ap_status s = score_mode(scores, &nu, &mu);
     if (s != AP_OK) return s;
     std::string why;
-    if (!choose_variant(w, nu, mu, groups, pl, &why))
+    if (!choose_variant(w, nu, mu, groups, step, pl, &why))
         return fail(AP_E_UNSUPPORTED, "%s", why.c_str());
-    const int64_t rows = std::max<int64_t>(0, m - w), cols = std::max<int64_t>(0, n - w);
+    // plot rows: x-windows 0, step, 2 step, ... below m - w
+    const int64_t rows = m > w ? (m - w + step - 1) / step : 0;
+    const int64_t cols = std::max<int64_t>(0, n - w);
     tile_plan(pl, rows, cols, chunk, current_device());
     return AP_OK;
 }
@@ -92,9 +95,10 @@ ap_status check_output(const Plan &pl, const void *x, const void *y, const void 
 
 namespace {
 
-ap_status make_plan(int64_t m, int64_t n, int32_t w, const ap_scores *scores, Plan *pl)
+ap_status make_plan(int64_t m, int64_t n, int32_t w, const ap_scores *scores, Plan *pl,
+                    int64_t step = 1)
 {
-    return plan_plot(m, n, w, scores, g_groups_override.load(), g_chunk_override.load(), pl);
+    return plan_plot(m, n, w, scores, g_groups_override.load(), g_chunk_override.load(), pl, step);
 }
 
 constexpr int64_t kBandBudget = 1LL << 30;   // bytes of banded plot per dots pass
@@ -201,6 +205,20 @@ ap_status ap_alignment_plot(const uint8_t *x, int64_t m, const uint8_t *y, int64
 {
     Plan pl;
     ap_status s = make_plan(m, n, w, scores, &pl);
+    if (s != AP_OK) return s;
+    s = check_output(pl, x, y, out, out_elem_bytes, ld);
+    if (s != AP_OK || pl.rows == 0 || pl.cols == 0) return s;
+    cudaError_t e = launch_comb(pl, x, m, y, n, out, out_elem_bytes, ld, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail_cuda(e, "strip comb launch");
+    return AP_OK;
+}
+
+ap_status ap_alignment_plot_step(const uint8_t *x, int64_t m, const uint8_t *y, int64_t n,
+                                 int32_t w, const ap_scores *scores, int64_t step, void *out,
+                                 int32_t out_elem_bytes, int64_t ld, void *stream)
+{
+    Plan pl;
+    ap_status s = make_plan(m, n, w, scores, &pl, step);
     if (s != AP_OK) return s;
     s = check_output(pl, x, y, out, out_elem_bytes, ld);
     if (s != AP_OK || pl.rows == 0 || pl.cols == 0) return s;

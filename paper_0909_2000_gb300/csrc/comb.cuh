@@ -80,6 +80,7 @@ struct CombParams {
     // turning them into ALU shifts; the ALU pipe is the comb's bottleneck.
     uint32_t one;
     uint32_t shmul[4];
+    int64_t step;       // x offset between consecutive plot rows (vertical step h)
 };
 
 // ---------------------------------------------------------------------------
@@ -344,6 +345,10 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
 //        NU = 1 is LCS
 // PADU   trailing units (rows for LCS, row groups of NU otherwise) of each
 //        thread that may be padding (never match)
+// XR     vertical step: plot row r is the x-window at r * step, so the NS
+//        strips of a register are not neighbours; each thread then keeps one
+//        x word per unit (gathered once per tile) and computes each unit's
+//        match mask directly instead of byte-shifting shared masks
 //
 // Each step combs two physical columns, interleaved row by row, so a thread
 // always has two independent dependency chains:
@@ -351,7 +356,7 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
 //   score: the '$' column and the character column of y' pair u (keys per pair).
 // Threads of a strip group are skewed by one step: thread g works on unit
 // u = s - g and takes its top seaweeds from thread g-1 by warp shuffle.
-template <class L, int R, int G, int NU, int MU, int PADU>
+template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
 __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64_t ch,
                                           uint32_t *ring)
 {
@@ -360,7 +365,7 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
     constexpr int NGRP = 32 / G;
     constexpr int SPW = NGRP * NS;                    // strips per warp
     constexpr int RP = R / NU;                        // x characters (units) per thread
-    constexpr int NQ = RP / L::RPW + 1;               // aligned x words
+    constexpr int NQ = XR ? RP : RP / L::RPW + 1;     // x words (aligned, or one per unit)
     static_assert(NU >= 1 && MU >= 0 && MU < NU && (NU > 1 || MU == 0), "bad blow-up");
     static_assert(R % (NU * L::RPW) == 0, "R must fill whole x words");
     static_assert(PADU <= RP, "padding window larger than the lane");
@@ -380,9 +385,10 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
     const int ub = (g * wk) / G;
     const int nreal = ((g + 1) * wk) / G - ub;
 
-    // Aligned x words of this thread's stream x[ig + ub ...].
+    // x words: the aligned words of this thread's stream x[ig + ub ...], or
+    // (vertical step) unit q's character of each of the NS strips.
     uint32_t xw[NQ];
-    {
+    if (!XR) {
         const int64_t base = ig + ub;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -392,6 +398,18 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
                 const int64_t idx = base + q * L::RPW + t;
                 const uint32_t c = (idx < p.m) ? (uint32_t)__ldg(p.x + idx) : 0u;
                 wv |= c << (L::BITS * t);
+            }
+            xw[q] = wv;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            uint32_t wv = 0;
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                const int64_t idx = (ig + b) * p.step + ub + q;
+                const uint32_t c = (idx < p.m) ? (uint32_t)__ldg(p.x + idx) : 0u;
+                wv |= c << (L::BITS * b);
             }
             xw[q] = wv;
         }
@@ -541,17 +559,25 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
             }
             const uint32_t yb0 = ychar(2 * u) * L::ONES;
             const uint32_t yb1 = ychar(2 * u + 1) * L::ONES;
-            uint32_t mm0[NQ], mm1[NQ];
+            uint32_t mm0[XR ? 1 : NQ], mm1[XR ? 1 : NQ];
+            if (!XR) {
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                mm0[q] = mismatch_mask<L>(xw[q], yb0, one);
-                mm1[q] = mismatch_mask<L>(xw[q], yb1, one);
+                for (int q = 0; q < NQ; ++q) {
+                    mm0[q] = mismatch_mask<L>(xw[q], yb0, one);
+                    mm1[q] = mismatch_mask<L>(xw[q], yb1, one);
+                }
             }
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 const int q = k / L::RPW, r = k % L::RPW;
-                uint32_t m0 = (r == 0) ? mm0[q] : row_shift(mm0[q], mm0[q + 1], shm(r));
-                uint32_t m1 = (r == 0) ? mm1[q] : row_shift(mm1[q], mm1[q + 1], shm(r));
+                uint32_t m0, m1;
+                if (XR) {
+                    m0 = mismatch_mask<L>(xw[k], yb0, one);
+                    m1 = mismatch_mask<L>(xw[k], yb1, one);
+                } else {
+                    m0 = (r == 0) ? mm0[q] : row_shift(mm0[q], mm0[q + 1], shm(r));
+                    m1 = (r == 0) ? mm1[q] : row_shift(mm1[q], mm1[q + 1], shm(r));
+                }
                 const int pi = k - (R - PADU);
                 if (pi >= 0) {
                     m0 |= padm[pi < 0 ? 0 : pi];
@@ -578,15 +604,18 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
                 }
             }
             const uint32_t yb = ychar(u) * L::ONES;
-            uint32_t mm[NQ];
+            uint32_t mm[XR ? 1 : NQ];
+            if (!XR) {
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) mm[q] = mismatch_mask<L>(xw[q], yb, one);
+                for (int q = 0; q < NQ; ++q) mm[q] = mismatch_mask<L>(xw[q], yb, one);
+            }
 #pragma unroll
             for (int q = 0; q < RP; ++q) {
                 const int pi = q - (RP - PADU);
                 const uint32_t pad = (pi >= 0) ? padm[pi < 0 ? 0 : pi] : 0u;
                 const int qq = q / L::RPW, r = q % L::RPW;
-                uint32_t mq = (r == 0) ? mm[qq] : row_shift(mm[qq], mm[qq + 1], shm(r));
+                uint32_t mq = XR ? mismatch_mask<L>(xw[q], yb, one)
+                                 : ((r == 0) ? mm[qq] : row_shift(mm[qq], mm[qq + 1], shm(r)));
                 if (pi >= 0) mq |= pad;
 #pragma unroll
                 for (int rho = 0; rho < NU; ++rho) {
@@ -652,7 +681,7 @@ __host__ __device__ constexpr int comb_warp_words(int ring)
 }
 
 // Plain launch: one warp per tile; tiles are numbered strip group fastest.
-template <class L, int R, int G, int NU, int MU, int PADU>
+template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, AP_MIN_BLOCKS)
 comb_kernel(CombParams p)
 {
@@ -660,7 +689,7 @@ comb_kernel(CombParams p)
     const int wid = threadIdx.x >> 5;
     const int64_t tile = p.tile0 + (int64_t)blockIdx.x * kWarpsPerBlock + wid;
     if (tile >= p.ntiles) return;
-    comb_tile<L, R, G, NU, MU, PADU>(p, tile % p.nsg, tile / p.nsg,
+    comb_tile<L, R, G, NU, MU, PADU, XR>(p, tile % p.nsg, tile / p.nsg,
                                     smem + wid * comb_warp_words<G>(p.ring));
 }
 
@@ -683,7 +712,7 @@ struct BatchParams {
 // Persistent launch over a batch: every warp takes the next tile of the work
 // list until it is exhausted.  Each tile is combed exactly as a plain launch
 // combs it, so results are bit-identical to one call per job.
-template <class L, int R, int G, int NU, int MU, int PADU>
+template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, AP_MIN_BLOCKS)
 comb_batch_kernel(BatchParams b)
 {
@@ -697,7 +726,7 @@ comb_batch_kernel(BatchParams b)
         t = __shfl_sync(0xffffffffu, t, 0);
         if ((int64_t)t >= b.ntiles) break;
         const BatchTile bt = b.tiles[t];
-        comb_tile<L, R, G, NU, MU, PADU>(b.jobs[bt.job], bt.sg, bt.ch, wsm);
+        comb_tile<L, R, G, NU, MU, PADU, XR>(b.jobs[bt.job], bt.sg, bt.ch, wsm);
         __syncwarp();
     }
 }

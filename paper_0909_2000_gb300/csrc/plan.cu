@@ -14,13 +14,13 @@ namespace {
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
-const Variant *find_variant(int key_bits, int rows, int groups, int nu, int mu)
+const Variant *find_variant(int key_bits, int rows, int groups, int nu, int mu, int xrows)
 {
     int count = 0;
     const Variant *t = variant_table(&count);
     for (int i = 0; i < count; ++i)
         if (t[i].key_bits == key_bits && t[i].rows == rows && t[i].groups == groups &&
-            t[i].nu == nu && t[i].mu == mu)
+            t[i].nu == nu && t[i].mu == mu && t[i].xrows == xrows)
             return &t[i];
     return nullptr;
 }
@@ -34,9 +34,11 @@ int next_pow2(int v)
 
 }  // namespace
 
-bool choose_variant(int w, int nu, int mu, int want_groups, Plan *pl, std::string *why)
+bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *pl,
+                    std::string *why)
 {
     const bool score = nu > 1;
+    const int xrows = step > 1 ? 1 : 0;
     // key_bits: 7 (w <= 120), 8 (LCS, w <= 254: values fit a byte), else 15.
     int kbits = 0, rows = 0, groups = 0;
     auto rows_for = [&](int g, int unit, int lo, int hi) -> bool {
@@ -48,7 +50,15 @@ bool choose_variant(int w, int nu, int mu, int want_groups, Plan *pl, std::strin
         rows = (int)r;
         return true;
     };
-    if (!score) {
+    if (xrows) {
+        // Vertical step: one x word per unit; LCS and {2,1,0} up to w = 120.
+        kbits = 7;
+        if (!score && w <= 120) {
+            if (!rows_for(1, 8, 8, 64)) rows_for(2, 4, 36, 60);
+        } else if (nu == 2 && mu == 1 && w <= 120) {
+            if (rows_for(4, 4, 4, 32)) rows *= 2;
+        }
+    } else if (!score) {
         if (w <= 120) {
             kbits = 7;
             if (want_groups == 2) rows_for(2, 4, 16, 60);
@@ -85,18 +95,20 @@ bool choose_variant(int w, int nu, int mu, int want_groups, Plan *pl, std::strin
             if (rows_for(8, 4, 4, 16)) rows *= nu;
         }
     }
-    const Variant *v = (rows > 0) ? find_variant(kbits, rows, groups, nu, mu) : nullptr;
+    const Variant *v = (rows > 0) ? find_variant(kbits, rows, groups, nu, mu, xrows) : nullptr;
     if (!v) {
         if (why) {
             char buf[160];
-            snprintf(buf, sizeof buf, "no compiled comb variant for w=%d with scores {%d,%d,0}",
-                     w, nu, mu);
+            snprintf(buf, sizeof buf,
+                     "no compiled comb variant for w=%d with scores {%d,%d,0} and step %lld", w, nu,
+                     mu, (long long)step);
             *why = buf;
         }
         return false;
     }
     pl->v = v;
     pl->w = w;
+    pl->step = step;
     pl->nu = nu;
     pl->mu = mu;
     pl->comb_rows = nu * w;
@@ -191,6 +203,7 @@ void fill_params(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y, 
     p->shmul[1] = 1u << 24;
     p->shmul[2] = 1u << 16;
     p->shmul[3] = 1u << 8;
+    p->step = pl.step;
 }
 
 cudaError_t raise_smem_limit(const void *fn)

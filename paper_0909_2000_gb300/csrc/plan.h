@@ -12,6 +12,7 @@ struct Plan {
     const Variant *v = nullptr;
     int w = 0;            // window length (key window)
     int nu = 1, mu = 0;   // score blow-up {nu, mu, 0}; nu = 1 is LCS
+    int64_t step = 1;     // vertical step: plot row r is the x-window at r * step
     int comb_rows = 0;    // physical comb height: nu * w
     int renorm = 0;       // steps between key renormalisations
     int ring = 0;         // exit-ring slots (power of two > w)
@@ -26,7 +27,8 @@ struct Plan {
 // Picks the variant for window w and score blow-up {nu, mu, 0}.  `groups` > 0
 // asks for that many threads per strip group (when a variant exists).
 // Returns false (with a message) when no compiled variant covers the request.
-bool choose_variant(int w, int nu, int mu, int groups, Plan *pl, std::string *why);
+bool choose_variant(int w, int nu, int mu, int groups, int64_t step, Plan *pl,
+                    std::string *why);
 
 // Tiles a rows x cols plot for the chosen variant.  `chunk_hint` > 0 forces
 // the column chunk (rounded up to a multiple of 32).

@@ -17,6 +17,7 @@ struct Variant {
     int rows;        // R: physical comb rows per thread
     int groups;      // G: threads per strip group
     int nu, mu;      // score blow-up {nu, mu, 0}; nu = 1 is LCS
+    int xrows;       // 1: vertical-step layout (one x word per unit)
     comb_fn_t fn;
     batch_fn_t batch_fn;
 };
@@ -27,6 +28,6 @@ const Variant *variant_table(int *count);
 }  // namespace ap
 
 // Instantiation helper: one template instance plus its registry entry.
-#define AP_VARIANT(LANES, KEYBITS, BITS, R, G, NU, MU, PADU)                        \
-    { KEYBITS, BITS, R, G, NU, MU, &ap::comb_kernel<ap::LANES, R, G, NU, MU, PADU>,     \
-      &ap::comb_batch_kernel<ap::LANES, R, G, NU, MU, PADU> }
+#define AP_VARIANT(LANES, KEYBITS, BITS, R, G, NU, MU, PADU, XR)                    \
+    { KEYBITS, BITS, R, G, NU, MU, XR, &ap::comb_kernel<ap::LANES, R, G, NU, MU, PADU, XR>, \
+      &ap::comb_batch_kernel<ap::LANES, R, G, NU, MU, PADU, XR> }

@@ -203,3 +203,29 @@ def test_dots_overflow_reports_full_count(cuda_lib):
     except ap.ApError as err:
         assert err.status == ap.AP_E_OVERFLOW
     assert np.array_equal(ap.dots_to_numpy(dots, 10), o[:10])
+
+
+STEP_CASES = [
+    (300, 260, 16, 2, (1, 0, 0)), (333, 290, 30, 5, (1, 0, 0)), (500, 410, 64, 3, (1, 0, 0)),
+    (600, 500, 100, 5, (1, 0, 0)), (420, 380, 120, 7, (1, 0, 0)), (250, 300, 20, 5, (2, 1, 0)),
+    (500, 430, 100, 5, (2, 1, 0)), (37, 60, 9, 4, (1, 0, 0)),
+]
+
+
+@pytest.mark.parametrize("m,n,w,step,scores", STEP_CASES)
+def test_vertical_step(cuda_lib, m, n, w, step, scores):
+    """Section 3's step h: only x-windows at multiples of h (rows [::h] of the plot)."""
+    ap = cuda_lib
+    seed = m + n + w + step
+    x = synth.dna(seed, 1, m)
+    y, _ = synth.plant(x, synth.dna(seed, 2, n), 1, min(m, n) // 3, seed, 3, synth.DNA, 0.1, 0.05)
+    o = oracle.plot(x, y, w, scores[0], scores[1])[::step]
+    g = ap.alignment_plot_step(dev(x), dev(y), w, step, scores, out_dtype=torch.int16)
+    torch.cuda.synchronize()
+    g = g.cpu().numpy().astype(np.int64)
+    assert g.shape == o.shape and np.array_equal(g, o), np.argwhere(g != o)[:4].tolist()
+    if step == 5:
+        # step 1 through the same entry point is the plain plot
+        g1 = ap.alignment_plot_step(dev(x), dev(y), w, 1, scores, out_dtype=torch.int16)
+        torch.cuda.synchronize()
+        assert np.array_equal(g1.cpu().numpy().astype(np.int64), oracle.plot(x, y, w, scores[0], scores[1]))
