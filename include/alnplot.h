@@ -175,6 +175,38 @@ ap_status ap_alignment_plot_step(const uint8_t *x, int64_t m, const uint8_t *y,
                                  int64_t ld, void *stream);
 
 /*
+ * Plot into HOST memory (and optionally its dots), end to end: x and y are
+ * HOST arrays (pinned memory copies fastest), `out` is a HOST buffer of
+ * (m - w) x ld elements, row-major, as in ap_alignment_plot.  The plot is
+ * combed band by band into two device band buffers, and each band's copy
+ * back to the host overlaps the comb of the next.  So the plot may be larger
+ * than device memory, and the copy hides behind the compute.  With ld equal
+ * to cols rounded up to a multiple of 32 (the device band's row stride),
+ * each band is one contiguous copy.
+ *
+ *   threshold, dots, dots_cap, dots_count: if dots_count is non-null, the
+ *     dots with P >= threshold are also returned (HOST `dots`, row-major as in
+ *     ap_alignment_dots; AP_E_OVERFLOW beyond dots_cap, full count reported);
+ *     pass dots_count = NULL for the plot alone.
+ *   workspace: DEVICE, >= ap_plot_host_workspace_size(...) bytes (the
+ *     sequences, two band buffers, row counts, and dots_cap dots).
+ *
+ * Synchronous: returns when the plot and dots are in host memory.  Errors as
+ * in ap_alignment_plot, plus AP_E_NOMEM for a short workspace.
+ */
+ap_status ap_plot_host_workspace_size(int64_t m, int64_t n, int32_t w,
+                                      const ap_scores *scores,
+                                      int32_t out_elem_bytes, int64_t dots_cap,
+                                      int64_t *bytes);
+ap_status ap_alignment_plot_host(const uint8_t *x, int64_t m, const uint8_t *y,
+                                 int64_t n, int32_t w, const ap_scores *scores,
+                                 void *out, int32_t out_elem_bytes, int64_t ld,
+                                 int32_t threshold, ap_dot *dots,
+                                 int64_t dots_cap, int64_t *dots_count,
+                                 void *workspace, int64_t workspace_bytes,
+                                 void *stream);
+
+/*
  * Bytes of device workspace ap_alignment_dots needs for these sizes.
  * bytes: host pointer, written on success.
  */

@@ -19,7 +19,7 @@ import threading
 
 __all__ = [
     "load", "ApError", "LCS", "SCORE", "plot_shape", "plot_plan", "alignment_plot",
-    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "alignment_plot_step", "set_chunk", "set_lanes_per_strip", "Batch", "Server", "DOT_DTYPE_FIELDS",
+    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "alignment_plot_step", "alignment_plot_host", "set_chunk", "set_lanes_per_strip", "Batch", "Server", "DOT_DTYPE_FIELDS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -101,6 +101,9 @@ def _declare(lib):
         "ap_plot_plan": [i64, i64, i32, sc, ctypes.POINTER(ap_plan)],
         "ap_alignment_plot": [p, i64, p, i64, i32, sc, p, i32, i64, p],
         "ap_alignment_plot_step": [p, i64, p, i64, i32, sc, i64, p, i32, i64, p],
+        "ap_plot_host_workspace_size": [i64, i64, i32, sc, i32, i64, i64p],
+        "ap_alignment_plot_host": [p, i64, p, i64, i32, sc, p, i32, i64, i32, p, i64, i64p, p, i64,
+                                   p],
         "ap_dots_workspace_size": [i64, i64, i32, sc, i64p],
         "ap_alignment_dots": [p, i64, p, i64, i32, sc, i32, p, i64, i64p, p, i64, p],
         "ap_plot_dots_workspace_size": [i64, i64p],
@@ -260,6 +263,50 @@ def alignment_plot_step(x, y, w: int, step: int, scores=LCS, out=None, out_dtype
                                          ctypes.c_void_p(out.data_ptr()), out.element_size(), ld,
                                          _stream_handle(stream)))
     return out
+
+
+def alignment_plot_host(x, y, w: int, scores=LCS, out=None, threshold=None,
+                        dots_cap: int = 1 << 22, workspace=None, stream=None):
+    """Plot into host memory end to end (ap_alignment_plot_host).
+
+    x, y: host uint8 arrays or CPU tensors (pinned copies fastest); ``out``: a
+    CPU uint8/16-bit tensor of at least (m-w, n-w), row-major, ideally pinned.
+    With a threshold, also returns the dots ((k, 3) int64 numpy array) and
+    their count.  Returns (out, dots, count)."""
+    import numpy as np
+    import torch
+    xt = torch.as_tensor(np.ascontiguousarray(x, dtype=np.uint8) if not isinstance(x, torch.Tensor) else x)
+    yt = torch.as_tensor(np.ascontiguousarray(y, dtype=np.uint8) if not isinstance(y, torch.Tensor) else y)
+    m, n = xt.numel(), yt.numel()
+    rows, cols = plot_shape(m, n, w)
+    sc = _scores(scores)
+    if out is None:
+        out = torch.empty((rows, cols), dtype=torch.uint8 if max(1, sc.match) * w <= 255 else torch.int16,
+                          pin_memory=torch.cuda.is_available())
+    lib = load()
+    cap = int(dots_cap) if threshold is not None else 0
+    need = ctypes.c_int64()
+    _check(lib.ap_plot_host_workspace_size(m, n, w, ctypes.byref(sc), out.element_size(), cap,
+                                           ctypes.byref(need)))
+    if workspace is None:
+        workspace = torch.empty(max(need.value, 1), dtype=torch.uint8, device="cuda")
+    dbuf = np.zeros((max(cap, 1), 3), dtype=np.uint32)
+    cnt = ctypes.c_int64()
+    ld = out.stride(0) if rows > 1 else max(cols, out.shape[1])
+    st = lib.ap_alignment_plot_host(ctypes.c_void_p(xt.data_ptr()), m, ctypes.c_void_p(yt.data_ptr()), n, w,
+                                    ctypes.byref(sc), ctypes.c_void_p(out.data_ptr()), out.element_size(), ld,
+                                    int(threshold if threshold is not None else 0),
+                                    ctypes.c_void_p(dbuf.ctypes.data), cap,
+                                    ctypes.byref(cnt) if threshold is not None else None,
+                                    ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                    _stream_handle(stream))
+    _check(st)
+    if threshold is None:
+        return out, None, 0
+    k = min(cnt.value, cap)
+    d = np.zeros((k, 3), dtype=np.int64)
+    d[:, 0], d[:, 1], d[:, 2] = dbuf[:k, 0], dbuf[:k, 1], dbuf[:k, 2] & 0xFFFF
+    return out, d, cnt.value
 
 
 def _dots_tensor(count: int, device):

@@ -1,0 +1,178 @@
+// host_plot.cu -- a plot (and its dots) computed into host memory, with the
+// device-to-host copy of each plot band overlapping the comb of the next.
+//
+// The plot rows are combed band by band into two device band buffers taken
+// from the caller's workspace.  Band b is combed on the caller's stream, its
+// dots (if asked for) are appended on the same stream, and a second stream
+// copies the band to the host plot while band b + 1 is combed into the other
+// buffer.  This keeps the GPU combing while the plot streams out, and it lets
+// the plot be larger than device memory.  (Combing alternate bands on two
+// streams was measured slower: the concurrent band kernels interfere.)
+#include <algorithm>
+#include <mutex>
+
+#include "alnplot_internal.h"
+#include "plan.h"
+
+namespace ap {
+namespace {
+
+constexpr int64_t kHostBand = 1LL << 30;     // bytes per device band buffer (several waves of tiles)
+
+int64_t align256(int64_t v) { return (v + 255) & ~(int64_t)255; }
+
+struct HostLayout {
+    int64_t band_rows = 0, band_ld = 0, x_off = 0, y_off = 0, buf_off[2] = {0, 0},
+            counts_off[2] = {0, 0}, offsets_off[2] = {0, 0}, running_off = 0, dots_off = 0,
+            total = 0;
+};
+
+HostLayout host_layout(const Plan &pl, int64_t m, int64_t n, int elem, int64_t dots_cap)
+{
+    HostLayout L;
+    L.band_ld = (pl.cols + 31) / 32 * 32;
+    const int64_t spw = pl.strips_per_warp;
+    int64_t br = kHostBand / std::max<int64_t>(1, L.band_ld * elem);
+    br = std::max<int64_t>(spw, br / spw * spw);
+    L.band_rows = std::min(br, (pl.rows + spw - 1) / spw * spw);
+    int64_t o = 0;
+    L.x_off = o;
+    o += align256(m);
+    L.y_off = o;
+    o += align256(n);
+    for (int k = 0; k < 2; ++k) {
+        L.buf_off[k] = o;
+        o += align256(L.band_rows * L.band_ld * elem);
+    }
+    for (int k = 0; k < 2; ++k) {
+        L.counts_off[k] = o;
+        o += align256(L.band_rows * 4);
+        L.offsets_off[k] = o;
+        o += align256(L.band_rows * 8);
+    }
+    L.running_off = o;
+    o += 256;
+    L.dots_off = o;
+    o += align256(std::max<int64_t>(0, dots_cap) * (int64_t)sizeof(ap_dot));
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+}  // namespace ap
+
+using namespace ap;
+
+extern "C" {
+
+ap_status ap_plot_host_workspace_size(int64_t m, int64_t n, int32_t w, const ap_scores *scores,
+                                      int32_t out_elem_bytes, int64_t dots_cap, int64_t *bytes)
+{
+    if (!bytes || (out_elem_bytes != 1 && out_elem_bytes != 2) || dots_cap < 0)
+        return fail(AP_E_INVAL, "ap_plot_host_workspace_size: bad argument");
+    Plan pl;
+    ap_status s = plan_plot(m, n, w, scores, 0, 0, &pl);
+    if (s != AP_OK) return s;
+    *bytes = host_layout(pl, m, n, out_elem_bytes, dots_cap).total;
+    return AP_OK;
+}
+
+ap_status ap_alignment_plot_host(const uint8_t *x, int64_t m, const uint8_t *y, int64_t n,
+                                 int32_t w, const ap_scores *scores, void *out,
+                                 int32_t out_elem_bytes, int64_t ld, int32_t threshold,
+                                 ap_dot *dots, int64_t dots_cap, int64_t *dots_count,
+                                 void *workspace, int64_t workspace_bytes, void *stream)
+{
+    Plan pl;
+    ap_status s = plan_plot(m, n, w, scores, 0, 0, &pl);
+    if (s != AP_OK) return s;
+    s = check_output(pl, x, y, out, out_elem_bytes, ld);
+    if (s != AP_OK) return s;
+    if (dots_cap < 0 || (dots_cap > 0 && !dots) || (dots_cap > 0 && !dots_count))
+        return fail(AP_E_INVAL, "ap_alignment_plot_host: bad dot buffer");
+    if (dots_count) *dots_count = 0;
+    if (pl.rows == 0 || pl.cols == 0) return AP_OK;
+    const HostLayout L = host_layout(pl, m, n, out_elem_bytes, dots_cap);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(AP_E_NOMEM, "workspace of %lld bytes given, %lld needed",
+                    (long long)workspace_bytes, (long long)L.total);
+    const bool want_dots = dots_count != nullptr;
+    char *ws = (char *)workspace;
+    uint8_t *dx = (uint8_t *)(ws + L.x_off), *dy = (uint8_t *)(ws + L.y_off);
+    int64_t *running = (int64_t *)(ws + L.running_off);
+    ap_dot *ddots = (ap_dot *)(ws + L.dots_off);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // the caller's stream combs every band; the copy stream moves them out
+    cudaStream_t cs[2] = {st, st}, copy = nullptr;
+    cudaEvent_t combed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr},
+                dotted[2] = {nullptr, nullptr};
+    cudaError_t e = cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&combed[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&dotted[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, (size_t)m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && want_dots) e = cudaMemsetAsync(running, 0, sizeof(int64_t), st);
+    int band = 0;
+    for (int64_t r0 = 0; r0 < pl.rows && e == cudaSuccess; r0 += L.band_rows, ++band) {
+        const int k = band & 1;
+        cudaStream_t sk = cs[k];
+        const int64_t br = std::min(L.band_rows, pl.rows - r0);
+        void *buf = ws + L.buf_off[k];
+        if (band >= 2) e = cudaStreamWaitEvent(sk, copied[k], 0);   // buffer k is free again
+        Plan bp = pl;
+        tile_plan(&bp, br, pl.cols, 0, current_device());
+        if (e == cudaSuccess)
+            e = launch_comb(bp, dx + r0, m - r0, dy, n, buf, out_elem_bytes, L.band_ld, sk);
+        if (e == cudaSuccess && want_dots) {
+            if (band >= 1) e = cudaStreamWaitEvent(sk, dotted[k ^ 1], 0);   // dots in band order (same stream: no-op)
+            if (e == cudaSuccess)
+                e = dots_pass(buf, out_elem_bytes, br, pl.cols, L.band_ld, threshold, r0, ddots,
+                              dots_cap, (int32_t *)(ws + L.counts_off[k]),
+                              (int64_t *)(ws + L.offsets_off[k]), running, sk);
+            if (e == cudaSuccess) e = cudaEventRecord(dotted[k], sk);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(combed[k], sk);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(copy, combed[k], 0);
+        char *dst = (char *)out + r0 * ld * out_elem_bytes;
+        if (e == cudaSuccess && ld == L.band_ld)      // same row stride: one contiguous copy
+            e = cudaMemcpyAsync(dst, buf, (size_t)(br * ld * out_elem_bytes), cudaMemcpyDeviceToHost,
+                                copy);
+        else if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(dst, (size_t)(ld * out_elem_bytes), buf,
+                                  (size_t)(L.band_ld * out_elem_bytes),
+                                  (size_t)(pl.cols * out_elem_bytes), (size_t)br,
+                                  cudaMemcpyDeviceToHost, copy);
+        if (e == cudaSuccess) e = cudaEventRecord(copied[k], copy);
+    }
+    int64_t total = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(copy);
+    if (e == cudaSuccess && want_dots) {
+        e = cudaMemcpyAsync(&total, running, sizeof total, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        const int64_t keep = std::min(total, dots_cap);
+        if (e == cudaSuccess && keep > 0)
+            e = cudaMemcpy(dots, ddots, (size_t)keep * sizeof(ap_dot), cudaMemcpyDeviceToHost);
+    } else if (e == cudaSuccess) {
+        e = cudaStreamSynchronize(st);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (combed[k]) cudaEventDestroy(combed[k]);
+        if (copied[k]) cudaEventDestroy(copied[k]);
+        if (dotted[k]) cudaEventDestroy(dotted[k]);
+    }
+    if (copy) cudaStreamDestroy(copy);
+    if (e != cudaSuccess) return fail_cuda(e, "ap_alignment_plot_host");
+    if (want_dots) {
+        *dots_count = total;
+        if (total > dots_cap)
+            return fail(AP_E_OVERFLOW, "%lld dots, buffer holds %lld", (long long)total,
+                        (long long)dots_cap);
+    }
+    return AP_OK;
+}
+
+}  // extern "C"

@@ -229,3 +229,23 @@ def test_vertical_step(cuda_lib, m, n, w, step, scores):
         g1 = ap.alignment_plot_step(dev(x), dev(y), w, 1, scores, out_dtype=torch.int16)
         torch.cuda.synchronize()
         assert np.array_equal(g1.cpu().numpy().astype(np.int64), oracle.plot(x, y, w, scores[0], scores[1]))
+
+
+@pytest.mark.parametrize("m,n,w,thr,scores", [(900, 700, 40, 28, (1, 0, 0)), (500, 650, 30, 45, (2, 1, 0)),
+                                              (3000, 2500, 100, 75, (1, 0, 0))])
+def test_plot_into_host_memory(cuda_lib, m, n, w, thr, scores):
+    """ap_alignment_plot_host: host sequences in, host plot and dots out, with
+    band copies overlapping the comb; equal to the device plot and dots."""
+    ap = cuda_lib
+    x = synth.dna(m, 1, m)
+    y, _ = synth.plant(x, synth.dna(n, 2, n), 2, min(m, n) // 4, 9, 3, synth.DNA, 0.1, 0.05)
+    out, dots, count = ap.alignment_plot_host(x, y, w, scores, threshold=thr)
+    dev_plot = ap.alignment_plot(dev(x), dev(y), w, scores, out_dtype=out.dtype)
+    torch.cuda.synchronize()
+    assert torch.equal(out, dev_plot.cpu())
+    want = oracle.dots(dev_plot.cpu().numpy().astype(np.int64), thr)
+    assert count == len(want) and np.array_equal(dots, want)
+    if m * n < 1_000_000:
+        assert np.array_equal(out.numpy().astype(np.int64), oracle.plot(x, y, w, scores[0], scores[1]))
+    plot_only, _, _ = ap.alignment_plot_host(x, y, w, scores)
+    assert torch.equal(plot_only, out)
