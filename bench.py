@@ -50,7 +50,7 @@ def parse_args():
                              "lcs_dna_20k_w100", "batch_dna_4096", "serve_dna_poisson",
                              "score_dna_80k_w100_step5"])
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
