@@ -290,7 +290,7 @@ def alignment_plot_host(x, y, w: int, scores=LCS, out=None, threshold=None,
                                            ctypes.byref(need)))
     if workspace is None:
         workspace = torch.empty(max(need.value, 1), dtype=torch.uint8, device="cuda")
-    dbuf = np.zeros((max(cap, 1), 3), dtype=np.uint32)
+    dbuf = np.empty((max(cap, 1), 3), dtype=np.uint32)   # the library fills the first count rows
     cnt = ctypes.c_int64()
     ld = out.stride(0) if rows > 1 else max(cols, out.shape[1])
     st = lib.ap_alignment_plot_host(ctypes.c_void_p(xt.data_ptr()), m, ctypes.c_void_p(yt.data_ptr()), n, w,
@@ -519,7 +519,7 @@ class Server:
         cnt = ctypes.c_int64()
         held = self._max_dots.get(ticket, 1 << 22)
         cap = held if cap is None else min(cap, held)
-        buf = np.zeros((max(cap, 1), 3), dtype=np.uint32)
+        buf = np.empty((max(cap, 1), 3), dtype=np.uint32)
         st = lib.ap_server_fetch(self._h, ticket, buf.ctypes.data, cap, ctypes.byref(cnt))
         if st not in (AP_OK, AP_E_OVERFLOW, AP_E_CANCELLED, AP_E_CUDA):
             raise ApError(st, lib.ap_last_error().decode())

@@ -266,7 +266,7 @@ ap_status ap_alignment_dots(const uint8_t *x, int64_t m, const uint8_t *y, int64
     for (int64_t r0 = 0; r0 < pl.rows; r0 += L.band_rows) {
         const int64_t br = std::min(L.band_rows, pl.rows - r0);
         Plan bp = pl;
-        tile_plan(&bp, br, pl.cols, pl.chunk, current_device());
+        tile_plan(&bp, br, pl.cols, g_chunk_override.load(), current_device());
         e = launch_comb(bp, x + r0, m - r0, y, n, band, L.elem, L.band_ld, st);
         if (e != cudaSuccess) return fail_cuda(e, "strip comb launch");
         e = dots_pass(band, L.elem, br, pl.cols, L.band_ld, threshold, r0, dots, cap, counts,

@@ -136,29 +136,61 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
     return true;
 }
 
-void tile_plan(Plan *pl, int64_t rows, int64_t cols, int64_t chunk_hint, int device)
+static int resident_warps(const Plan &pl, int device)
 {
-    pl->rows = rows;
-    pl->cols = cols;
-    pl->nsg = ceil_div(rows, pl->strips_per_warp);
-    int sms = 152;
+    // Warps of this variant resident on the whole GPU at once (from the
+    // occupancy calculator), or 8 per SM on a 152-SM part when no device is
+    // available (host-only planning).
+    int sms = 152, per_sm = 0;
     if (device >= 0) {
         int v = 0;
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && v > 0)
             sms = v;
         else
             cudaGetLastError();
+        if (pl.v && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        &per_sm, (const void *)pl.v->fn, kWarpsPerBlock * 32, pl.smem) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 0;
+        }
     }
+    const int warps_per_sm = per_sm > 0 ? per_sm * kWarpsPerBlock : 8;
+    return sms * warps_per_sm;
+}
+
+void tile_plan(Plan *pl, int64_t rows, int64_t cols, int64_t chunk_hint, int device)
+{
+    pl->rows = rows;
+    pl->cols = cols;
+    pl->nsg = ceil_div(rows, pl->strips_per_warp);
     int64_t chunk;
     if (chunk_hint > 0) {
         chunk = round_up(chunk_hint, kOB);
     } else {
-        // Enough tiles for several waves of ~8 resident warps per SM, but
-        // chunks long enough that the w - 1 warm-up columns stay small.
-        const int64_t want_tiles = (int64_t)sms * 8 * 4;
-        const int64_t nch = std::max<int64_t>(1, ceil_div(want_tiles, pl->nsg));
-        chunk = round_up(ceil_div(cols, nch), kOB);
-        chunk = std::max<int64_t>(chunk, round_up(16 * (int64_t)pl->w, kOB));
+        // All tiles of a launch take the same time, so the launch lasts
+        // ceil(tiles / resident warps) rounds of one tile each, and a tile
+        // combs its chunk plus the w - 1 warm-up columns (plus a few columns'
+        // worth of setup).  Pick the chunk count that minimises
+        //     ceil(nsg * nch / S) * (chunk(nch) + w - 1 + setup):
+        // few chunks waste the last, partly filled round; many chunks pay
+        // the warm-up again and again.
+        const int64_t S = resident_warps(*pl, device);
+        const int64_t setup = 8;
+        const int64_t max_nch = std::max<int64_t>(1, ceil_div(std::max<int64_t>(cols, 1), kOB));
+        int64_t best_nch = 1;
+        double best = -1.0;
+        for (int64_t nch = 1; nch <= max_nch; ++nch) {
+            const int64_t ch = round_up(ceil_div(std::max<int64_t>(cols, 1), nch), kOB);
+            if (ceil_div(std::max<int64_t>(cols, 1), ch) != nch) continue;   // same as a smaller count
+            const int64_t rounds = ceil_div(pl->nsg * nch, S);
+            const double cost = (double)rounds * (double)(ch + pl->w - 1 + setup);
+            if (best < 0.0 || cost < best * (1.0 - 1e-9)) {
+                best = cost;
+                best_nch = nch;
+            }
+            if (rounds > 64 * ceil_div(pl->nsg, S) + 64) break;   // far past any useful split
+        }
+        chunk = round_up(ceil_div(std::max<int64_t>(cols, 1), best_nch), kOB);
     }
     chunk = std::min<int64_t>(chunk, round_up(std::max<int64_t>(cols, 1), kOB));
     chunk = std::min<int64_t>(chunk, 1LL << 30);   // tile-local indices are 32-bit
