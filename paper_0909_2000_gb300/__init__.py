@@ -304,8 +304,8 @@ def alignment_plot_host(x, y, w: int, scores=LCS, out=None, threshold=None,
     if threshold is None:
         return out, None, 0
     k = min(cnt.value, cap)
-    d = np.zeros((k, 3), dtype=np.int64)
-    d[:, 0], d[:, 1], d[:, 2] = dbuf[:k, 0], dbuf[:k, 1], dbuf[:k, 2] & 0xFFFF
+    d = dbuf[:k].astype(np.int64)
+    d[:, 2] &= 0xFFFF          # value, without the pad half-word
     return out, d, cnt.value
 
 
@@ -525,10 +525,8 @@ class Server:
             raise ApError(st, lib.ap_last_error().decode())
         self._max_dots.pop(ticket, None)
         k = min(cnt.value, cap)
-        out = np.zeros((k, 3), dtype=np.int64)
-        out[:, 0] = buf[:k, 0]
-        out[:, 1] = buf[:k, 1]
-        out[:, 2] = buf[:k, 2] & 0xFFFF
+        out = buf[:k].astype(np.int64)
+        out[:, 2] &= 0xFFFF        # value, without the pad half-word
         return st, cnt.value, out
 
     def cancel(self, ticket: int) -> None:

@@ -6,8 +6,12 @@
 // dots (if asked for) are appended on the same stream, and a second stream
 // copies the band to the host plot while band b + 1 is combed into the other
 // buffer.  This keeps the GPU combing while the plot streams out, and it lets
-// the plot be larger than device memory.  (Combing alternate bands on two
-// streams was measured slower: the concurrent band kernels interfere.)
+// the plot be larger than device memory.  Two arrangements were measured
+// slower:
+// * combing alternate bands on two streams (the concurrent band kernels
+//   interfere);
+// * the dots on the copy stream (they wait for SMs held by the next band's
+//   comb, and the band copy waits behind them).
 #include <algorithm>
 #include <mutex>
 
@@ -105,13 +109,11 @@ ap_status ap_alignment_plot_host(const uint8_t *x, int64_t m, const uint8_t *y, 
 
     // the caller's stream combs every band; the copy stream moves them out
     cudaStream_t cs[2] = {st, st}, copy = nullptr;
-    cudaEvent_t combed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr},
-                dotted[2] = {nullptr, nullptr};
+    cudaEvent_t combed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
     cudaError_t e = cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         e = cudaEventCreateWithFlags(&combed[k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[k], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&dotted[k], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, (size_t)m, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, (size_t)n, cudaMemcpyHostToDevice, st);
@@ -127,14 +129,10 @@ ap_status ap_alignment_plot_host(const uint8_t *x, int64_t m, const uint8_t *y, 
         tile_plan(&bp, br, pl.cols, 0, current_device());
         if (e == cudaSuccess)
             e = launch_comb(bp, dx + r0, m - r0, dy, n, buf, out_elem_bytes, L.band_ld, sk);
-        if (e == cudaSuccess && want_dots) {
-            if (band >= 1) e = cudaStreamWaitEvent(sk, dotted[k ^ 1], 0);   // dots in band order (same stream: no-op)
-            if (e == cudaSuccess)
-                e = dots_pass(buf, out_elem_bytes, br, pl.cols, L.band_ld, threshold, r0, ddots,
-                              dots_cap, (int32_t *)(ws + L.counts_off[k]),
-                              (int64_t *)(ws + L.offsets_off[k]), running, sk);
-            if (e == cudaSuccess) e = cudaEventRecord(dotted[k], sk);
-        }
+        if (e == cudaSuccess && want_dots)      // dots in band order on the compute stream
+            e = dots_pass(buf, out_elem_bytes, br, pl.cols, L.band_ld, threshold, r0, ddots,
+                          dots_cap, (int32_t *)(ws + L.counts_off[k]),
+                          (int64_t *)(ws + L.offsets_off[k]), running, sk);
         if (e == cudaSuccess) e = cudaEventRecord(combed[k], sk);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(copy, combed[k], 0);
         char *dst = (char *)out + r0 * ld * out_elem_bytes;
@@ -150,19 +148,17 @@ ap_status ap_alignment_plot_host(const uint8_t *x, int64_t m, const uint8_t *y, 
     }
     int64_t total = 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize(copy);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && want_dots) {
         e = cudaMemcpyAsync(&total, running, sizeof total, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         const int64_t keep = std::min(total, dots_cap);
         if (e == cudaSuccess && keep > 0)
             e = cudaMemcpy(dots, ddots, (size_t)keep * sizeof(ap_dot), cudaMemcpyDeviceToHost);
-    } else if (e == cudaSuccess) {
-        e = cudaStreamSynchronize(st);
     }
     for (int k = 0; k < 2; ++k) {
         if (combed[k]) cudaEventDestroy(combed[k]);
         if (copied[k]) cudaEventDestroy(copied[k]);
-        if (dotted[k]) cudaEventDestroy(dotted[k]);
     }
     if (copy) cudaStreamDestroy(copy);
     if (e != cudaSuccess) return fail_cuda(e, "ap_alignment_plot_host");
