@@ -29,7 +29,8 @@ def _variants():
     kernel.  (nu, mu) is the score blow-up {nu, mu, 0}; (1, 0) is LCS."""
     v = []
     # LCS, 7-bit keys in 8-bit lanes, one thread per strip group: w <= 120
-    for r in range(8, 121, 8):
+    # (rows in steps of 4, one x word, so that R - w <= 3 padding rows)
+    for r in range(8, 121, 4):
         v.append(("U8Lanes", 7, 8, r, 1, 1, 0, 8))
     # LCS, 7-bit keys, a strip group's rows split over 2 or 4 threads
     for g, rs in ((2, range(16, 61, 4)), (4, range(8, 33, 4))):

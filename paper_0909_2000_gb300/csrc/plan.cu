@@ -63,7 +63,7 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
             kbits = 7;
             if (want_groups == 2) rows_for(2, 4, 16, 60);
             else if (want_groups == 4) rows_for(4, 4, 8, 32);
-            if (!rows) rows_for(1, 8, 8, 120);
+            if (!rows) rows_for(1, 4, 8, 120);
         } else if (w <= 254) {
             kbits = 8;
             if (want_groups == 4 || !rows_for(2, 64, 64, 64)) rows_for(4, 4, 32, 64);
