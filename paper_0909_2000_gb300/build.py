@@ -66,8 +66,8 @@ def _variants():
         v.append(("U8Lanes", 7, 8, r, 1, 1, 0, 8, True))
     for r in range(36, 61, 4):
         v.append(("U8Lanes", 7, 8, r, 2, 1, 0, 8, True))
-    for rp in range(4, 33, 4):
-        v.append(("U8Lanes", 7, 8, 2 * rp, 4, 2, 1, 4, True))
+    for rp in range(2, 33, 2):
+        v.append(("U8Lanes", 7, 8, 2 * rp, 4, 2, 1, min(4, rp), True))
     return v
 
 

@@ -367,7 +367,8 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
     constexpr int RP = R / NU;                        // x characters (units) per thread
     constexpr int NQ = XR ? RP : RP / L::RPW + 1;     // x words (aligned, or one per unit)
     static_assert(NU >= 1 && MU >= 0 && MU < NU && (NU > 1 || MU == 0), "bad blow-up");
-    static_assert(R % (NU * L::RPW) == 0, "R must fill whole x words");
+    static_assert(XR ? (R % NU == 0) : (R % (NU * L::RPW) == 0),
+                  "R must fill whole units (vertical step) or whole x words");
     static_assert(PADU <= RP, "padding window larger than the lane");
 
     const int lane = threadIdx.x & 31;

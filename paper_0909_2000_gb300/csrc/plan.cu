@@ -56,7 +56,7 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
         if (!score && w <= 120) {
             if (!rows_for(1, 8, 8, 64)) rows_for(2, 4, 36, 60);
         } else if (nu == 2 && mu == 1 && w <= 120) {
-            if (rows_for(4, 4, 4, 32)) rows *= 2;
+            if (rows_for(4, 2, 2, 32)) rows *= 2;
         }
     } else if (!score) {
         if (w <= 120) {
