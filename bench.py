@@ -92,11 +92,19 @@ def cores():
         return os.cpu_count() or 1
 
 
+ARM_PARTS = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1",
+             "0xd49": "Arm Neoverse-N2", "0xd8e": "Arm Neoverse-N3", "0xd84": "Arm Neoverse-V3"}
+
+
 def cpu_model():
+    """The host CPU's model name (x86 'model name', or the Arm part number
+    mapped to its core name)."""
     try:
         for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part", "hardware")):
-                return line.split(":", 1)[1].strip()
+            key = line.split(":", 1)[0].strip().lower()
+            if key in ("model name", "cpu part", "hardware"):
+                v = line.split(":", 1)[1].strip()
+                return "%s (%s)" % (ARM_PARTS[v], v) if v in ARM_PARTS else v
     except OSError:
         pass
     return "unknown"
