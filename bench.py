@@ -636,7 +636,7 @@ def main():
 
     e2e = None
     if not args.no_e2e and rank == 0:
-        e2e = measure_e2e(ap, c, scores, thr, dev, min(args.steps, 3))
+        e2e = measure_e2e(ap, c, scores, thr, dev, min(args.steps, 5))
 
     line = {
         "metric": "window-pair cells/sec (m*n*w/s)",

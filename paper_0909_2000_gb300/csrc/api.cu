@@ -115,7 +115,7 @@ DotsLayout dots_layout(const Plan &pl)
 {
     DotsLayout L;
     L.elem = pl.max_value > 255 ? 2 : 1;
-    L.band_ld = (pl.cols + 15) / 16 * 16;
+    L.band_ld = (pl.cols + 31) / 32 * 32;   // whole 32-byte sectors per row block
     const int64_t spw = pl.strips_per_warp;
     const int64_t all_rows = (pl.rows + spw - 1) / spw * spw;
     int64_t br = kBandBudget / std::max<int64_t>(1, L.band_ld * L.elem);
