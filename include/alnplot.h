@@ -48,7 +48,8 @@ typedef enum ap_status {
 
 /*
  * Alignment scores, normalised so that gap = 0 and 0 <= mismatch < match
- * (Section 2: "LCS corresponds to match 1, mismatch 0, gap 0").  Supported:
+ * (Section 2: LCS is the scheme with match 1 and mismatch and gap 0).
+ * Supported:
  *   {1, 0, 0}  LCS: P = LLCS of the two windows, 0 <= P <= w.
  *   {2, 1, 0}  Section 2's scheme (match 1, mismatch 0, gap -1/2), shifted
  *              so gaps score 0 and doubled: P = T = S + w, w <= T <= 2w,
@@ -56,10 +57,11 @@ typedef enum ap_status {
  *              '$'-interleaved windows (Section 2), with Definition 3.2's
  *              (w, 2) restriction.
  *   {m, x, 0}  2 <= m <= 4, 1 <= x < m: the same construction for other small
- *              rational scores (Section 2: "a constant factor blow-up of the
- *              input strings"): every character becomes x copies of '$'
- *              followed by m - x copies of itself, and P = the LCS of the
- *              blown-up windows = the best alignment score, x w <= P <= m w.
+ *              rational scores (Section 2 reduces them to LCS by enlarging
+ *              the input strings by a constant factor): every character
+ *              becomes x copies of '$' followed by m - x copies of itself,
+ *              and P = the LCS of the blown-up windows = the best alignment
+ *              score, x w <= P <= m w.
  *              Windows up to 32 (8-bit lanes) or 128 (16-bit lanes).
  * A scheme (a, b, g) with g < 0 maps to {a - 2g, b - 2g, 0} after scaling to
  * integers (and the plot value to S - 2wg).  Other normalised pairs, and
@@ -160,9 +162,9 @@ ap_status ap_alignment_plot(const uint8_t *x, int64_t m, const uint8_t *y,
                             void *stream);
 
 /*
- * Alignment plot with a vertical step (Section 3: "introducing a step size
- * h, and only comparing w-windows starting at positions that are multiples
- * of h"; Section 4 uses h = 5): plot row r holds the x-window starting at
+ * Alignment plot with a vertical step (Section 3: a step size h keeps only
+ * the x-windows whose start is a multiple of h; Section 4 uses h = 5): plot
+ * row r holds the x-window starting at
  * r * step, for 0 <= r < ceil((m - w) / step), against every y-window:
  *     out[r*ld + j] = P[r * step][j]
  * step = 1 is ap_alignment_plot.  With step > 1 this build covers LCS and
