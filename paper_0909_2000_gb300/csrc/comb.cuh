@@ -56,7 +56,7 @@ constexpr int kWarpsPerBlock = 4;
 #ifndef AP_MIN_BLOCKS
 #define AP_MIN_BLOCKS 1   // minimum resident blocks per SM asked of the compiler
 #endif
-constexpr int kOB = 32;   // plot columns staged per flush (one per lane)
+constexpr int kOB = 32;   // plot columns staged per flush (one per lane; a power of two)
 
 struct CombParams {
     const uint8_t *x;
@@ -261,27 +261,55 @@ __device__ __forceinline__ uint32_t renorm_key(uint32_t k, uint32_t rr_bias, uin
 // of group grp's strips (one per lane).  The warp writes `cnt` columns
 // starting at plot column jbase for its SPW strip rows.
 //
-// Byte plots from one-thread strip groups, in full blocks of kOB = 32
-// columns into 16-byte aligned rows, take 16-byte stores: two threads pack
-// 16 columns each of one row.  Measured against 4-byte stores on 100k DNA
-// plots: w = 16: 21.9 -> 19.2 ms, w = 32: 38.5 -> 34.8 ms, w = 100:
-// 89.2 -> 87.6 ms.  (The same scheme for 16-bit values and all group sizes
-// in one routine cost registers and was slower.)  Other blocks use 4-byte
-// (8-bit) or 8-byte (16-bit) stores, 8 threads per row and 4 rows per pass,
-// or a scalar path; each store instruction writes whole 32-byte sectors.
+// One-thread strip groups with 8-bit lanes write full blocks of kOB = 32
+// columns into 16-byte aligned rows with 16-byte stores:
+// * byte plots (LCS kernels): two threads pack 16 columns each of one row;
+//   measured against 4-byte stores on 100k DNA plots, w = 16: 21.9 -> 19.2
+//   ms, w = 32: 38.5 -> 34.8 ms, w = 100: 89.2 -> 87.6 ms;
+// * 16-bit plots (score kernels, WIDE): four threads pack 8 columns each;
+//   the 20k protein score plot went 6.20 -> 6.05 ms.
+// (One routine for both widths and all group sizes cost registers and was
+// slower.)  Other blocks use 4-byte (8-bit) or 8-byte (16-bit) stores, 8
+// threads per row and 4 rows per pass, or a scalar path; each store
+// instruction writes whole 32-byte sectors.
 template <class L>
 __device__ __forceinline__ uint32_t lane_of(uint32_t w, int b)
 {
     return (w >> (L::BITS * b)) & L::MASK;
 }
 
-template <class L, int NGRP>
+template <class L, int NGRP, bool WIDE = false>
 __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t *stage,
                                             int64_t iw, int64_t jbase, int cnt, int lane)
 {
     constexpr int NS = L::NS;
     constexpr int SPW = NGRP * NS;
-    if (L::BITS == 8 && NGRP == 32 && p.out_bytes == 1 && cnt == kOB &&
+    if (WIDE && L::BITS == 8 && NGRP == 32 && p.out_bytes == 2 && cnt == kOB &&
+        ((((uintptr_t)p.out) | (uintptr_t)(2 * p.ld)) & 15u) == 0) {
+        // byte values widened to 16 bits: four threads per row (8 columns
+        // each), 8 rows per pass
+        const int part = lane & 3, rp = lane >> 2;
+#pragma unroll 1
+        for (int it = 0; it < SPW / 8; ++it) {
+            const int rw = it * 8 + rp;
+            const int64_t i = iw + rw;
+            const int grp = rw / NS;
+            const uint32_t b = (uint32_t)(rw % NS);
+            const uint32_t *sp = stage + (8 * part) * (NGRP + 1) + grp;
+            uint32_t wv[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) wv[c] = sp[c * (NGRP + 1)];
+            const uint32_t sel = b | ((b + 4u) << 4);
+            uint32_t o4[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o4[k] = prmt(prmt(wv[2 * k], wv[2 * k + 1], sel), 0u, 0x4140u);
+            if (i < p.rows)
+                *(uint4 *)((uint16_t *)p.out + i * p.ld + jbase + 8 * part) =
+                    make_uint4(o4[0], o4[1], o4[2], o4[3]);
+        }
+        return;
+    }
+    if (!WIDE && L::BITS == 8 && NGRP == 32 && p.out_bytes == 1 && cnt == kOB &&
         ((((uintptr_t)p.out) | (uintptr_t)p.ld) & 15u) == 0) {
         // two threads per row (16 columns each), 16 rows per pass
         const int half = lane & 1, rp = lane >> 1;
@@ -516,11 +544,17 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
             // (col - age) mod ring per lane (the ring has 256 slots with full keys)
             const uint32_t slots = L::FULL ? sub_lanes<L>(colb, age)
                                            : (colb + L::MSB - age) & ring_maskv;
+            // every byte of slots is already a slot number (< ring), and
+            // every byte of valid is 0 or 1: one byte permute extracts each
+            // (LCS; the score kernels keep shifts, which cost them fewer
+            // registers)
 #pragma unroll
             for (int b = 0; b < NS; ++b) {
-                const uint32_t slot = (slots >> (8 * b)) & (uint32_t)ring_mask;
+                const uint32_t slot = SCORE ? (slots >> (8 * b)) & (uint32_t)ring_mask
+                                            : prmt(slots, 0u, 0x4440u | (uint32_t)b);
                 uint8_t *e = ring8 + slot * (uint32_t)(NGRP * 4) + b;
-                const uint8_t f = (uint8_t)((valid >> (8 * b)) & 1u);
+                const uint8_t f = SCORE ? (uint8_t)((valid >> (8 * b)) & 1u)
+                                        : (uint8_t)prmt(valid, 0u, 0x4440u | (uint32_t)b);
                 if (SCORE) *e = (uint8_t)(*e + f);
                 else *e = f;
             }
@@ -544,16 +578,22 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
         }
     };
     auto stage_out = [&](int col) {
-        if (col >= wk - 1 && col < ncomb)
-            stage[((col - (wk - 1)) % kOB) * (NGRP + 1) + grp] = wvec - d;
+        if (col >= wk - 1 && col < ncomb) {
+            // col >= w - 1 here, so the two forms agree; each is the one that
+            // measured faster for its kernel family (register allocation)
+            const int jj = SCORE ? (col - (wk - 1)) % kOB
+                                 : (int)((uint32_t)(col - (wk - 1)) & (kOB - 1));
+            stage[jj * (NGRP + 1) + grp] = wvec - d;
+        }
     };
     auto maybe_flush = [&](int col) {       // uniform across the warp
         if (col >= wk - 1 && col < ncomb) {
             const int jo = col - (wk - 1);
-            if ((jo % kOB) == kOB - 1 || jo == plot_cols - 1) {
+            const int jm = SCORE ? jo % kOB : (jo & (kOB - 1));   // jo >= 0
+            if (jm == kOB - 1 || jo == plot_cols - 1) {
                 __syncwarp();
-                const int cnt = (jo % kOB) + 1;
-                flush_stage<L, NGRP>(p, stage, iw, c0 + jo - (cnt - 1), cnt, lane);
+                const int cnt = jm + 1;
+                flush_stage<L, NGRP, (NU > 1)>(p, stage, iw, c0 + jo - (cnt - 1), cnt, lane);
                 __syncwarp();
             }
         }
