@@ -188,9 +188,15 @@ __device__ __forceinline__ uint32_t mismatch_word(uint32_t xw, uint32_t yb, uint
 }
 
 // Full-lane mismatch mask of one aligned word: 0xFF.. in lanes where x != y.
-template <class L>
+// When x ^ y can never have the lane's top bit, (x ^ y) + LOW alone flags
+// the mismatches (one logic instruction fewer):
+// * 16-bit lanes: the characters are bytes;
+// * ST (same top bit): every character the tile compares is below 128, or
+//   every one is at least 128 (checked per tile by tile_same_top).
+template <class L, bool ST = false>
 __device__ __forceinline__ uint32_t mismatch_mask(uint32_t xw, uint32_t yb, uint32_t one)
 {
+    if (ST || L::BITS == 16) return prmt(mad_lo(xw ^ yb, one, L::LOW), 0u, L::SIGNREP);
     return prmt(mismatch_word<L>(xw, yb, one), 0u, L::SIGNREP);
 }
 
@@ -417,7 +423,7 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
 //   score: the '$' column and the character column of y' pair u (keys per pair).
 // Threads of a strip group are skewed by one step: thread g works on unit
 // u = s - g and takes its top seaweeds from thread g-1 by warp shuffle.
-template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
+template <class L, int R, int G, int NU, int MU, int PADU, bool XR, bool ST = false>
 __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64_t ch,
                                           uint32_t *ring)
 {
@@ -637,8 +643,8 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
             if (!XR) {
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
-                    mm0[q] = mismatch_mask<L>(xw[q], yb0, one);
-                    mm1[q] = mismatch_mask<L>(xw[q], yb1, one);
+                    mm0[q] = mismatch_mask<L, ST>(xw[q], yb0, one);
+                    mm1[q] = mismatch_mask<L, ST>(xw[q], yb1, one);
                 }
             }
 #pragma unroll
@@ -646,8 +652,8 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
                 const int q = k / L::RPW, r = k % L::RPW;
                 uint32_t m0, m1;
                 if (XR) {
-                    m0 = mismatch_mask<L>(xw[k], yb0, one);
-                    m1 = mismatch_mask<L>(xw[k], yb1, one);
+                    m0 = mismatch_mask<L, ST>(xw[k], yb0, one);
+                    m1 = mismatch_mask<L, ST>(xw[k], yb1, one);
                 } else {
                     m0 = (r == 0) ? mm0[q] : row_shift(mm0[q], mm0[q + 1], shm(r));
                     m1 = (r == 0) ? mm1[q] : row_shift(mm1[q], mm1[q + 1], shm(r));
@@ -681,14 +687,14 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
             uint32_t mm[XR ? 1 : NQ];
             if (!XR) {
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) mm[q] = mismatch_mask<L>(xw[q], yb, one);
+                for (int q = 0; q < NQ; ++q) mm[q] = mismatch_mask<L, ST>(xw[q], yb, one);
             }
 #pragma unroll
             for (int q = 0; q < RP; ++q) {
                 const int pi = q - (RP - PADU);
                 const uint32_t pad = (pi >= 0) ? padm[pi < 0 ? 0 : pi] : 0u;
                 const int qq = q / L::RPW, r = q % L::RPW;
-                uint32_t mq = XR ? mismatch_mask<L>(xw[q], yb, one)
+                uint32_t mq = XR ? mismatch_mask<L, ST>(xw[q], yb, one)
                                  : ((r == 0) ? mm[qq] : row_shift(mm[qq], mm[qq + 1], shm(r)));
                 if (pi >= 0) mq |= pad;
 #pragma unroll
@@ -754,6 +760,50 @@ __host__ __device__ constexpr int comb_warp_words(int ring)
     return ring * (32 / G) + kOB * (32 / G + 1);
 }
 
+// True if every character the tile compares has the same top bit (all
+// below 128, or all at least 128): the x positions of its strips' windows
+// and the y positions of its columns and warm-up.  Warp-uniform; it reads
+// about (chunk + w) / 32 bytes per lane, once per tile.
+template <class L, int G>
+__device__ __forceinline__ bool tile_same_top(const CombParams &p, int64_t sg, int64_t ch)
+{
+    constexpr int SPW = (32 / G) * L::NS;
+    const int lane = threadIdx.x & 31;
+    const int64_t iw = sg * SPW;
+    const int64_t c0 = ch * p.chunk;
+    const int64_t c1 = (c0 + p.chunk < p.cols) ? c0 + p.chunk : p.cols;
+    const int64_t x1 = (iw + SPW + p.w - 1 < p.m) ? iw + SPW + p.w - 1 : p.m;
+    const int64_t y1 = (c1 + p.w - 1 < p.n) ? c1 + p.w - 1 : p.n;
+    uint32_t o = 0u, a = 0xFFu;
+    for (int64_t i = iw + lane; i < x1; i += 32) {
+        const uint32_t c = __ldg(p.x + i);
+        o |= c;
+        a &= c;
+    }
+    for (int64_t j = c0 + lane; j < y1; j += 32) {
+        const uint32_t c = __ldg(p.y + j);
+        o |= c;
+        a &= c;
+    }
+    o = __reduce_or_sync(0xffffffffu, o);
+    a = __reduce_and_sync(0xffffffffu, a);
+    return (o & 0x80u) == 0u || (a & 0x80u) != 0u;
+}
+
+// 8-bit-lane tiles (not the vertical-step layout) whose characters allow it
+// comb with the short mismatch test; the rest take the general one.
+// Measured on the 100k DNA plot, w = 100: 85.5 -> 82.5 ms.
+template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
+__device__ __forceinline__ void comb_tile_dispatch(const CombParams &p, int64_t sg, int64_t ch,
+                                                   uint32_t *ring)
+{
+    constexpr bool FAST_OK = L::BITS == 8 && !XR;
+    if (FAST_OK && tile_same_top<L, G>(p, sg, ch))
+        comb_tile<L, R, G, NU, MU, PADU, XR, FAST_OK>(p, sg, ch, ring);
+    else
+        comb_tile<L, R, G, NU, MU, PADU, XR, false>(p, sg, ch, ring);
+}
+
 // Plain launch: one warp per tile; tiles are numbered strip group fastest.
 template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, AP_MIN_BLOCKS)
@@ -763,8 +813,8 @@ comb_kernel(CombParams p)
     const int wid = threadIdx.x >> 5;
     const int64_t tile = p.tile0 + (int64_t)blockIdx.x * kWarpsPerBlock + wid;
     if (tile >= p.ntiles) return;
-    comb_tile<L, R, G, NU, MU, PADU, XR>(p, tile % p.nsg, tile / p.nsg,
-                                    smem + wid * comb_warp_words<G>(p.ring));
+    comb_tile_dispatch<L, R, G, NU, MU, PADU, XR>(p, tile % p.nsg, tile / p.nsg,
+                                                 smem + wid * comb_warp_words<G>(p.ring));
 }
 
 // One tile of a batch: which job, and which strip group and column chunk.
@@ -800,7 +850,7 @@ comb_batch_kernel(BatchParams b)
         t = __shfl_sync(0xffffffffu, t, 0);
         if ((int64_t)t >= b.ntiles) break;
         const BatchTile bt = b.tiles[t];
-        comb_tile<L, R, G, NU, MU, PADU, XR>(b.jobs[bt.job], bt.sg, bt.ch, wsm);
+        comb_tile_dispatch<L, R, G, NU, MU, PADU, XR>(b.jobs[bt.job], bt.sg, bt.ch, wsm);
         __syncwarp();
     }
 }

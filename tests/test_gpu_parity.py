@@ -123,6 +123,34 @@ def test_all_byte_values_and_identical_windows(cuda_lib):
             assert np.array_equal(g, o), (w, sc)
 
 
+@pytest.mark.parametrize("case", ["high", "split", "one_high_y"])
+def test_top_bit_of_the_alphabet(cuda_lib, case):
+    """Tiles whose characters all share the top bit take the short mismatch
+    test; the others the general one.  Alphabets entirely at or above 128,
+    and mixes across the tiles of one plot, against the oracle."""
+    ap = cuda_lib
+    hi = bytes([0xC1, 0xC3, 0xC7, 0xF0])
+    if case == "high":                      # every tile: all characters >= 128
+        x = synth.alphabet_string(5, 1, 700, list(hi))
+        y = synth.alphabet_string(5, 2, 900, list(hi))
+    elif case == "split":                   # x high, y low: tiles mix top bits
+        x = synth.alphabet_string(5, 3, 700, list(hi))
+        y = synth.alphabet_string(5, 4, 900, [0x41, 0x43, 0x47, 0x70])
+    else:                                   # one character >= 128 in an ASCII y
+        x = synth.dna(5, 5, 300)
+        y = synth.dna(5, 6, 3000)
+        y[1600] = 0xC1
+    set_chunk = ap.set_chunk
+    try:
+        set_chunk(256)                      # several column chunks: some tiles see it
+        for w, sc in ((40, (1, 0, 0)), (100, (1, 0, 0)), (150, (1, 0, 0)), (50, (2, 1, 0))):
+            o = oracle.plot(x, y, w, sc[0], sc[1])
+            g = gpu_plot(ap, x, y, w, sc, torch.int16)
+            assert np.array_equal(g, o), (case, w, sc)
+    finally:
+        set_chunk(0)
+
+
 def test_empty_and_degenerate(cuda_lib):
     ap = cuda_lib
     x = dev(synth.dna(2, 1, 10))
