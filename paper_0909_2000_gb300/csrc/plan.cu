@@ -69,8 +69,11 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
             if (want_groups == 4 || !rows_for(2, 64, 64, 64)) rows_for(4, 4, 32, 64);
         } else {
             kbits = 15;
-            for (int g : {2, 4, 8})
-                if (rows_for(g, 8, 16, 64)) break;
+            if (want_groups == 2 || want_groups == 4 || want_groups == 8)
+                rows_for(want_groups, 8, 16, 64);
+            if (!rows)
+                for (int g : {2, 4, 8})
+                    if (rows_for(g, 8, 16, 64)) break;
         }
     } else if (nu == 2 && mu == 1) {
         if (w <= 64) {
