@@ -449,10 +449,13 @@ def bench_serve(args):
     def cells(p):
         return float(max(0, len(p.x) - p.w)) * max(0, len(p.y) - p.w) * p.w
 
-    def run(rate, seconds, seed):
+    def run(rate, seconds, seed, check=None):
         reqs = synth.serving_requests(seed, rate=rate, duration=seconds)
         srv = ap.Server(mem_budget=64 << 30, max_slots=args.serve_slots)
         tickets = [None] * len(reqs)
+        # a seeded set of moderate requests whose dots are kept for checking
+        small = [k for k, (_, p) in enumerate(reqs) if cells(p) < 5e11]
+        keep = set(small[int(i)] for i in synth.below(seed, 77, 12, len(small))) if (check is not None and small) else set()
         t0 = time.perf_counter()
 
         def submitter():
@@ -465,13 +468,14 @@ def bench_serve(args):
         thr = th.Thread(target=submitter)
         thr.start()
         thr.join()
-        statuses = []
-        ndots = 0
-        for t in tickets:
-            statuses.append(srv.wait(t, -1))
-            st, cnt, _ = srv.fetch(t, cap=0)
-            ndots += cnt
+        statuses = [srv.wait(t, -1) for t in tickets]
         wall = time.perf_counter() - t0
+        ndots = 0
+        for k, t in enumerate(tickets):
+            st, cnt, dots = srv.fetch(t, cap=None if k in keep else 0)
+            ndots += cnt
+            if k in keep:
+                check.append((reqs[k][1], dots))
         stats = srv.stats()
         srv.close()
         total = sum(cells(p) for _, p in reqs)
@@ -488,11 +492,38 @@ def bench_serve(args):
     overload = run(args.serve_rate, args.serve_seconds, 0)
     capacity = overload["throughput_cells_per_s"]
     sust_rate = max(1.0, 0.7 * capacity / overload["mean_cells_per_request"])
-    sustained = run(sust_rate, max(10.0, args.serve_seconds), 1)
+    checked = []
+    sustained = run(sust_rate, max(10.0, args.serve_seconds), 1, checked)
     clk = clocks.stop()
+    # served dots against the plain call and the oracle (outside the timing):
+    # identical dot lists, every sampled dot's value, and sampled non-dots
+    # below the threshold
+    import oracle
+    dev = torch.device("cuda", 0)
+    same, oracle_ok, nsamp = True, True, 0
+    for k, (p, dots) in enumerate(checked):
+        pd, pc = ap.alignment_dots(torch.from_numpy(p.x).to(dev), torch.from_numpy(p.y).to(dev), p.w,
+                                   p.threshold)
+        plain = ap.dots_to_numpy(pd, pc)
+        same &= bool(np.array_equal(plain, dots))
+        rows, cols = max(0, len(p.x) - p.w), max(0, len(p.y) - p.w)
+        if rows == 0 or cols == 0:
+            continue
+        pick = dots[synth.below(9, 2 * k, min(200, len(dots)), len(dots))] if len(dots) else dots[:0]
+        ii = synth.below(9, 2 * k + 1, 200, rows)
+        jj = synth.below(9, 2 * k + 1000, 200, cols)
+        dotset = set(map(tuple, dots[:, :2].tolist()))
+        off = np.array([(i, j) for i, j in zip(ii, jj) if (int(i), int(j)) not in dotset], dtype=np.int64)
+        if len(pick):
+            want = oracle.samples(p.x, p.y, p.w, pick[:, 0], pick[:, 1])
+            oracle_ok &= bool(np.array_equal(want, pick[:, 2])) and bool((pick[:, 2] >= p.threshold).all())
+            nsamp += len(pick)
+        if len(off):
+            v = oracle.samples(p.x, p.y, p.w, off[:, 0], off[:, 1])
+            oracle_ok &= bool((v < p.threshold).all())
+            nsamp += len(off)
     # plain form: the same kind of requests, one ap_alignment_dots call after another
     reqs = synth.serving_requests(2, rate=args.serve_rate, duration=1.0)[:60]
-    dev = torch.device("cuda", 0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _, p in reqs:
@@ -515,6 +546,8 @@ def bench_serve(args):
         "offered_over_capacity": overload["offered_cells_per_s"] / capacity,
         "plain_sequential_dots": {"requests": len(reqs), "cells_per_s": plain_rate},
         "served_over_plain": capacity / plain_rate,
+        "parity": {"requests_checked": len(checked), "identical_to_plain_calls": same,
+                   "oracle_samples_ok": oracle_ok, "oracle_samples": nsamp},
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
