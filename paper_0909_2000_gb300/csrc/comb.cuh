@@ -761,9 +761,10 @@ __host__ __device__ constexpr int comb_warp_words(int ring)
 }
 
 // True if every character the tile compares has the same top bit (all
-// below 128, or all at least 128): the x positions of its strips' windows
-// and the y positions of its columns and warm-up.  Warp-uniform; it reads
-// about (chunk + w) / 32 bytes per lane, once per tile.
+// below 128, or all at least 128): the x positions from its first strip's
+// window to its last strip's (with a vertical step, the gaps between them
+// too) and the y positions of its columns and warm-up.  Warp-uniform; it
+// reads about (chunk + w) / 32 bytes per lane, once per tile.
 template <class L, int G>
 __device__ __forceinline__ bool tile_same_top(const CombParams &p, int64_t sg, int64_t ch)
 {
@@ -772,10 +773,11 @@ __device__ __forceinline__ bool tile_same_top(const CombParams &p, int64_t sg, i
     const int64_t iw = sg * SPW;
     const int64_t c0 = ch * p.chunk;
     const int64_t c1 = (c0 + p.chunk < p.cols) ? c0 + p.chunk : p.cols;
-    const int64_t x1 = (iw + SPW + p.w - 1 < p.m) ? iw + SPW + p.w - 1 : p.m;
+    const int64_t xe = (iw + SPW - 1) * p.step + p.w;      // past the last strip's window
+    const int64_t x1 = (xe < p.m) ? xe : p.m;
     const int64_t y1 = (c1 + p.w - 1 < p.n) ? c1 + p.w - 1 : p.n;
     uint32_t o = 0u, a = 0xFFu;
-    for (int64_t i = iw + lane; i < x1; i += 32) {
+    for (int64_t i = iw * p.step + lane; i < x1; i += 32) {
         const uint32_t c = __ldg(p.x + i);
         o |= c;
         a &= c;
@@ -790,14 +792,14 @@ __device__ __forceinline__ bool tile_same_top(const CombParams &p, int64_t sg, i
     return (o & 0x80u) == 0u || (a & 0x80u) != 0u;
 }
 
-// 8-bit-lane tiles (not the vertical-step layout) whose characters allow it
-// comb with the short mismatch test; the rest take the general one.
-// Measured on the 100k DNA plot, w = 100: 85.5 -> 82.5 ms.
+// 8-bit-lane tiles whose characters allow it comb with the short mismatch
+// test; the rest take the general one.  Measured on the 100k DNA plot,
+// w = 100: 85.5 -> 82.5 ms.
 template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
 __device__ __forceinline__ void comb_tile_dispatch(const CombParams &p, int64_t sg, int64_t ch,
                                                    uint32_t *ring)
 {
-    constexpr bool FAST_OK = L::BITS == 8 && !XR;
+    constexpr bool FAST_OK = L::BITS == 8;
     if (FAST_OK && tile_same_top<L, G>(p, sg, ch))
         comb_tile<L, R, G, NU, MU, PADU, XR, FAST_OK>(p, sg, ch, ring);
     else

@@ -147,6 +147,10 @@ def test_top_bit_of_the_alphabet(cuda_lib, case):
             o = oracle.plot(x, y, w, sc[0], sc[1])
             g = gpu_plot(ap, x, y, w, sc, torch.int16)
             assert np.array_equal(g, o), (case, w, sc)
+            if w <= 100:                    # the vertical-step layout too
+                gs = ap.alignment_plot_step(dev(x), dev(y), w, 3, sc, out_dtype=torch.int16)
+                torch.cuda.synchronize()
+                assert np.array_equal(gs.cpu().numpy().astype(np.int64), o[::3]), (case, w, sc, 3)
     finally:
         set_chunk(0)
 
