@@ -61,6 +61,10 @@ def test_host_side_validation_without_gpu():
     with pytest.raises(ap.ApError) as e:
         ap.plot_plan(100000, 100000, 600)
     assert e.value.status == ap.AP_E_UNSUPPORTED
+    for w, sc in ((513, ap.LCS), (257, ap.SCORE)):    # one past the largest windows built
+        with pytest.raises(ap.ApError) as e:
+            ap.plot_plan(2000, 2000, w, sc)
+        assert e.value.status == ap.AP_E_UNSUPPORTED
     with pytest.raises(ap.ApError):
         ap.set_chunk(-1)
 

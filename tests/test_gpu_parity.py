@@ -60,6 +60,11 @@ CASES = [
     (600, 640, 200, b"AC", (2, 1, 0)),
     (600, 620, 254, b"ACGT", (2, 1, 0)),
     (620, 640, 255, b"ACGT", (2, 1, 0)),
+    # the largest windows built: LCS w = 512 (16-bit lanes, 8 threads of 64
+    # rows), {2,1,0} w = 256 (8 threads of 32 pairs)
+    (700, 680, 512, b"ACGT", (1, 0, 0)),
+    (690, 700, 511, b"AC", (1, 0, 0)),
+    (560, 600, 256, b"ACGT", (2, 1, 0)),
 ]
 
 
