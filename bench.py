@@ -668,8 +668,8 @@ def main():
     traffic = profile_traffic("comb/" + c.name)
 
     e2e = None
-    if not args.no_e2e and rank == 0:
-        e2e = measure_e2e(ap, c, scores, thr, dev, min(args.steps, 5))
+    if not args.no_e2e:
+        e2e = measure_e2e(ap, c, scores, thr, dev, min(args.steps, 5), dist, world)
 
     line = {
         "metric": "window-pair cells/sec (m*n*w/s)",
@@ -709,30 +709,41 @@ def main():
     return 0
 
 
-def measure_e2e(ap, c, scores, thr, dev, steps):
+def measure_e2e(ap, c, scores, thr, dev, steps, dist=None, world=1):
     """Same metric through the public API from and to host memory:
     ap_alignment_plot_host copies x, y in from pinned host memory, combs the
     plot band by band and copies every band (and the dots) back while the
-    next band is combed.  Timed per call, every byte moved inside."""
+    next band is combed.  Timed per call, every byte moved inside.  Under
+    torchrun every rank runs its own calls between barriers; the step time
+    is the slowest rank's and the value counts all ranks' cells."""
     import torch
     m, n, w = len(c.x), len(c.y), c.w
     rows, cols = ap.plot_shape(m, n, w)
     score = scores == ap.SCORE
-    hx = torch.from_numpy(c.x).pin_memory()
-    hy = torch.from_numpy(c.y).pin_memory()
     dt = torch.int16 if score else torch.uint8
     ld = (cols + 31) // 32 * 32          # the device bands' row stride: contiguous copies
-    hout = torch.empty((rows, ld), dtype=dt, pin_memory=True)[:, :cols]
+    try:
+        hx = torch.from_numpy(c.x).pin_memory()
+        hy = torch.from_numpy(c.y).pin_memory()
+        hout = torch.empty((rows, ld), dtype=dt, pin_memory=True)[:, :cols]
+        ok = 1.0
+    except RuntimeError:                 # no room to pin the host plot on this rank
+        ok = 0.0
+    # every rank goes on only if all could pin their buffers (no rank waits alone)
+    if -max_over_ranks(-ok, dist, dev) < 1.0:
+        return None
     out, dots, count = ap.alignment_plot_host(hx, hy, w, scores, out=hout, threshold=thr)   # warm-up
     ts = []
     for _ in range(steps):
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         t0 = time.perf_counter()
         out, dots, count = ap.alignment_plot_host(hx, hy, w, scores, out=hout, threshold=thr)
-        ts.append(time.perf_counter() - t0)
+        ts.append(max_over_ranks((time.perf_counter() - t0) * 1e3, dist, dev) / 1e3)
     t = statistics.median(ts)
-    return {"value": float(m) * n * w / t, "unit": "cells/s", "h2d_bytes_per_step": m + n,
-            "d2h_bytes_per_step": rows * ld * hout.element_size() + (count or 0) * 12 + 8,
+    return {"value": float(m) * n * w * world / t, "unit": "cells/s", "h2d_bytes_per_step": (m + n) * world,
+            "d2h_bytes_per_step": (rows * ld * hout.element_size() + (count or 0) * 12 + 8) * world,
             "ms_per_step": t * 1e3, "steps": steps,
             "api": "ap_alignment_plot_host (band copies overlap the comb)"}
 
