@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 INT32_LANES_PER_SM_CLK = 128      # 32-bit integer lanes per SM per clock (GB300)
 SM_MAX_MHZ = 2070.0               # maximum SM clock of a GB300
-ALG_OPS_PER_CELL = 6.0 / 4.0      # 6 lane-ops per cell, 4 lanes per 32-bit op
+LANE_OPS_PER_CELL = 6.0           # the paper's vector step: 6 lane-ops per comb cell
 
 
 def parse_args():
@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lcs_dna_100k_w100",
                     choices=["lcs_dna_100k_w100", "lcs_dna_512_w16", "score_protein_20k_w64",
-                             "lcs_dna_20k_w100", "batch_dna_4096", "serve_dna_poisson",
+                             "lcs_dna_20k_w100", "lcs_dna_20k_w256", "batch_dna_4096", "serve_dna_poisson",
                              "score_dna_80k_w100_step5"])
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -67,7 +67,15 @@ def workload(name):
         return synth.dna_plot_512(0)
     if name == "lcs_dna_20k_w100":
         return synth.dna_plot_20k(0)
+    if name == "lcs_dna_20k_w256":
+        return synth.dna_plot_20k_w256(0)
     return synth.protein_score_20k(0)
+
+
+def wide(c):
+    """True for a uint16 plot: score plots (as the 20k protein workload
+    specifies) and plots whose values reach match * w > 255."""
+    return tuple(c.scores[:2]) != (1, 0) or c.scores[0] * c.w > 255
 
 
 def describe(c):
@@ -76,12 +84,12 @@ def describe(c):
     return {
         "workload": c.name, "m": len(c.x), "n": len(c.y), "w": c.w,
         "scores": "match 2, mismatch 1, gap 0" if score else "LCS (match 1, mismatch 0, gap 0)",
-        "output": "full %dx%d %s plot in HBM%s" % (rows, cols, "uint16" if score else "uint8",
+        "output": "full %dx%d %s plot in HBM%s" % (rows, cols, "uint16" if wide(c) else "uint8",
                                                   "" if c.threshold is None else
                                                   " + row-major dots >= %d" % c.threshold),
         "inputs": "seeded synthetic (SplitMix64), resident in HBM",
         "l2": "output %.2f GB per step >> 129 MB L2; L2 flushed (256 MB write) before every timed step"
-              % (rows * cols * (2 if score else 1) / 1e9),
+              % (rows * cols * (2 if wide(c) else 1) / 1e9),
     }
 
 
@@ -593,7 +601,7 @@ def main():
     plan = ap.plot_plan(m, n, w, scores)
     x = torch.from_numpy(c.x).to(dev)
     y = torch.from_numpy(c.y).to(dev)
-    out = ap.empty_plot(rows, cols, torch.int16 if score else torch.uint8, dev)
+    out = ap.empty_plot(rows, cols, torch.int16 if wide(c) else torch.uint8, dev)
     thr = c.threshold
     ws = torch.empty(max(ap.plot_dots_workspace_size(rows), 1), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -659,7 +667,8 @@ def main():
 
     # roofline of the comb kernel (integer ALU)
     comb_cells = float(rows) * (n - 1) * (2 * w if score else w) * (2 if score else 1)
-    alg_ops = comb_cells * ALG_OPS_PER_CELL
+    # 32-bit ops per cell: 6 lane-ops over the lanes of one register (4 or 2)
+    alg_ops = comb_cells * LANE_OPS_PER_CELL / plan["strips_per_reg"]
     comb_s = statistics.mean(comb_ms) / 1e3
     achieved = alg_ops / comb_s / 1e12
     props = torch.cuda.get_device_properties(dev)
@@ -675,7 +684,8 @@ def main():
         "metric": "window-pair cells/sec (m*n*w/s)",
         "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u8" if not score else "u8 keys, u16 out",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("u%d" % plan["lane_bits"]) + (", u16 out" if wide(c) and plan["lane_bits"] == 8 else ""),
         "data": "synthetic", "config": describe(c),
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
@@ -719,8 +729,7 @@ def measure_e2e(ap, c, scores, thr, dev, steps, dist=None, world=1):
     import torch
     m, n, w = len(c.x), len(c.y), c.w
     rows, cols = ap.plot_shape(m, n, w)
-    score = scores == ap.SCORE
-    dt = torch.int16 if score else torch.uint8
+    dt = torch.int16 if wide(c) else torch.uint8
     ld = (cols + 31) // 32 * 32          # the device bands' row stride: contiguous copies
     try:
         hx = torch.from_numpy(c.x).pin_memory()

@@ -184,6 +184,15 @@ def dna_plot_20k(seed: int = 0) -> Pair:
     return c
 
 
+def dna_plot_20k_w256(seed: int = 0) -> Pair:
+    """The 20k DNA recipe at w = 256, the serving mix's largest window: 16-bit
+    keys and a uint16 plot (values reach 256); dots >= ceil(0.8 w) = 205."""
+    c = dna_plot_100k(seed, 20_000, 20_000, 256, 4, 2000)
+    c.threshold = threshold_08(256)
+    c.name = "lcs_dna_20k_w256"
+    return c
+
+
 def protein_score_20k(seed: int = 0, m: int = 20_000, n: int = 20_000, w: int = 64) -> Pair:
     """Score plot (match 2, mismatch 1, gap 0), uniform 20-letter protein,
     m = n = 20,000, w = 64, uint16 output."""
