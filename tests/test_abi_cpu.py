@@ -100,3 +100,23 @@ def test_plan_of_the_100k_plot():
     assert pl["lane_bits"] == 8 and pl["strips_per_reg"] == 4 and pl["lanes_per_strip"] == 1
     # warm-up and padding overhead stay small
     assert pl["physical_cells"] < 1.06 * pl["logical_cells"]
+
+
+def test_chunk_count_minimises_rounds_times_tile_length():
+    """tile_plan's choice (host-only planning assumes 152 SMs x 8 warps): the
+    chunk count minimises ceil(tiles / S) * (chunk + w - 1 + 8) over every
+    count that gives a distinct 32-aligned chunk."""
+    S = 152 * 8
+    for m, n, w in ((100_000, 100_000, 100), (20_000, 20_000, 100), (512, 512, 16),
+                    (100_000, 100_000, 16), (3000, 90_000, 64)):
+        pl = ap.plot_plan(m, n, w)
+        rows, cols = ap.plot_shape(m, n, w)
+        nsg = -(-rows // (pl["strips_per_reg"] * 32 // pl["lanes_per_strip"]))
+
+        def cost(ch):
+            nch = -(-cols // ch)
+            return -(-(nsg * nch) // S) * (ch + w - 1 + 8)
+        chunks = {-(-(-(-cols // k)) // 32) * 32 for k in range(1, cols // 32 + 2)}
+        best = min(cost(ch) for ch in chunks)
+        assert pl["chunk"] % 32 == 0
+        assert cost(pl["chunk"]) <= best * (1 + 1e-9), (m, n, w, pl["chunk"])
