@@ -46,6 +46,12 @@ def _variants():
     v.append(("U8FLanes", 8, 8, 64, 2, 1, 0, 8))
     for r in range(32, 65, 4):
         v.append(("U8FLanes", 8, 8, r, 4, 1, 0, 8))
+    # LCS, 9-bit keys in 10-bit lanes (three strips per register), rows split
+    # over 4 or 8 threads: 256 < w <= 480
+    for r in range(66, 97, 3):
+        v.append(("U10Lanes", 9, 10, r, 4, 1, 0, 8))
+    for r in range(33, 61, 3):
+        v.append(("U10Lanes", 9, 10, r, 8, 1, 0, 8))
     # LCS, 15-bit keys in 16-bit lanes, rows split over 2, 4 or 8 threads: w <= 512
     for g in (2, 4, 8):
         for r in range(16, 65, 8):

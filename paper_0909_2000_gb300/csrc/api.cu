@@ -188,7 +188,7 @@ ap_status ap_plot_plan(int64_t m, int64_t n, int32_t w, const ap_scores *scores,
     ap_status s = make_plan(m, n, w, scores, &pl);
     if (s != AP_OK) return s;
     out->lane_bits = pl.v->lane_bits;
-    out->strips_per_reg = pl.v->lane_bits == 8 ? 4 : 2;
+    out->strips_per_reg = pl.v->lane_bits == 8 ? 4 : (pl.v->lane_bits == 10 ? 3 : 2);
     out->rows_per_lane = pl.v->rows;
     out->lanes_per_strip = pl.v->groups;
     out->comb_rows = pl.comb_rows;

@@ -80,6 +80,13 @@ struct CombParams {
     // turning them into ALU shifts; the ALU pipe is the comb's bottleneck.
     uint32_t one;
     uint32_t shmul[4];
+    // Row shifts of 10-bit lanes (three per register, bits 30-31 unused):
+    // rows r = 1, 2 past an aligned word are (a >> 10r) | (b << (30 - 10r)),
+    // the high word of a * shmul[r] plus b * shlo[r] (for byte lanes
+    // shlo = shmul).  spread_hi = 2^23 and spread_lo = 0x3FF turn the
+    // compare bits of 10-bit lanes into full-lane masks on the FMA pipe.
+    uint32_t shlo[4];
+    uint32_t spread_hi, spread_lo;
     int64_t step;       // x offset between consecutive plot rows (vertical step h)
 };
 
@@ -113,6 +120,22 @@ struct U8FLanes {
     static constexpr uint32_t LOW = 0x7F7F7F7Fu;
     static constexpr uint32_t SIGNREP = 0xBA98u;
     static constexpr uint32_t MASK = 0xFFu;
+};
+
+// 10-bit lanes (windows 257..480): three strips per register in bits 0-29,
+// 9-bit keys with bit 9 of each lane as the compare bit.  No byte permute
+// spreads a 10-bit lane, so masks are spread by two multiplies (FMA pipe).
+struct U10Lanes {
+    static constexpr int NS = 3;
+    static constexpr int BITS = 10;
+    static constexpr bool FULL = false;
+    static constexpr int RPW = 3;
+    static constexpr int KMAX = 511;
+    static constexpr uint32_t ONES = 0x00100401u;
+    static constexpr uint32_t MSB = 0x20080200u;
+    static constexpr uint32_t LOW = 0x1FF7FDFFu;
+    static constexpr uint32_t SIGNREP = 0u;         // not used
+    static constexpr uint32_t MASK = 0x3FFu;
 };
 
 struct U16Lanes {
@@ -167,14 +190,26 @@ __device__ __forceinline__ uint32_t sub_lanes(uint32_t a, uint32_t b)
     return lo ^ ((a ^ ~b) & L::MSB);
 }
 
+// Full-lane mask from each lane's compare bit (the other bits are junk):
+// one byte permute for 8- and 16-bit lanes; for 10-bit lanes the compare
+// bits are isolated and multiplied out, (t & MSB) / 2^9 * 0x3FF, as a high
+// and a low multiply with run-time factors (FMA pipe).
+template <class L>
+__device__ __forceinline__ uint32_t spread(uint32_t t, uint32_t sph, uint32_t spl)
+{
+    if (L::BITS == 10) return mad_lo(mul_hi(t & L::MSB, sph), spl, 0u);
+    return prmt(t, 0u, L::SIGNREP);
+}
+
 // Row register for rows r = 1..RPW-1 past an aligned word: the lanes start r
 // characters further into the x stream, i.e. the 64-bit pair (b:a) shifted
 // right by 8r bits = (a >> 8r) | (b << (32 - 8r)).  Both halves are integer
 // multiplies by s = 2^(32 - 8r) (high and low word), so the shift runs on the
 // FMA pipe and leaves the ALU pipe to the cells.
-__device__ __forceinline__ uint32_t row_shift(uint32_t a, uint32_t b, uint32_t s)
+// (For 10-bit lanes the low-word factor is 2^(30 - 10r), a separate s_lo.)
+__device__ __forceinline__ uint32_t row_shift(uint32_t a, uint32_t b, uint32_t s, uint32_t s_lo)
 {
-    return mad_lo(b, s, mul_hi(a, s));
+    return mad_lo(b, s_lo, mul_hi(a, s));
 }
 
 // Mismatch flags of one aligned word: lane MSB set iff x != y (any byte
@@ -190,14 +225,15 @@ __device__ __forceinline__ uint32_t mismatch_word(uint32_t xw, uint32_t yb, uint
 // Full-lane mismatch mask of one aligned word: 0xFF.. in lanes where x != y.
 // When x ^ y can never have the lane's top bit, (x ^ y) + LOW alone flags
 // the mismatches (one logic instruction fewer):
-// * 16-bit lanes: the characters are bytes;
+// * 10- and 16-bit lanes: the characters are bytes;
 // * ST (same top bit): every character the tile compares is below 128, or
 //   every one is at least 128 (checked per tile by tile_same_top).
 template <class L, bool ST = false>
-__device__ __forceinline__ uint32_t mismatch_mask(uint32_t xw, uint32_t yb, uint32_t one)
+__device__ __forceinline__ uint32_t mismatch_mask(uint32_t xw, uint32_t yb, uint32_t one,
+                                                  uint32_t sph, uint32_t spl)
 {
-    if (ST || L::BITS == 16) return prmt(mad_lo(xw ^ yb, one, L::LOW), 0u, L::SIGNREP);
-    return prmt(mismatch_word<L>(xw, yb, one), 0u, L::SIGNREP);
+    if (ST || L::BITS != 8) return spread<L>(mad_lo(xw ^ yb, one, L::LOW), sph, spl);
+    return spread<L>(mismatch_word<L>(xw, yb, one), sph, spl);
 }
 
 // One comb cell on NS strips at once.
@@ -217,16 +253,17 @@ __device__ __forceinline__ uint32_t mismatch_mask(uint32_t xw, uint32_t yb, uint
 // match is folded in as hm = 0xFF in match lanes (>= any key) and the swap
 // decision is the full-width compare hm >= v.
 template <class L>
-__device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t mm, uint32_t neg1)
+__device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t mm, uint32_t neg1,
+                                     uint32_t sph, uint32_t spl)
 {
     uint32_t M;
     if (L::FULL) {
         const uint32_t hm = h | ~mm;
         M = prmt(ge_lanes<L>(hm, v, neg1), 0u, L::SIGNREP);
     } else {
-        const uint32_t hc = h | ~mm | L::MSB;
+        const uint32_t hc = h | ~mm | L::MSB;   // (10-bit lanes: bits 30-31 are junk, never read)
         const uint32_t t = mad_lo(v, neg1, hc);  // hc - v
-        M = prmt(t, 0u, L::SIGNREP);
+        M = spread<L>(t, sph, spl);
     }
     const uint32_t vn = (h & M) | (v & ~M);
     h = h ^ v ^ vn;
@@ -235,10 +272,11 @@ __device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t mm, uint
 
 // Mismatch cell (no match possible): swap iff h >= v.
 template <class L>
-__device__ __forceinline__ void cell_mismatch(uint32_t &h, uint32_t &v, uint32_t neg1)
+__device__ __forceinline__ void cell_mismatch(uint32_t &h, uint32_t &v, uint32_t neg1,
+                                              uint32_t sph, uint32_t spl)
 {
-    const uint32_t t = L::FULL ? ge_lanes<L>(h, v, neg1) : h - v + L::MSB;
-    const uint32_t M = prmt(t, 0u, L::SIGNREP);
+    const uint32_t M = L::FULL ? prmt(ge_lanes<L>(h, v, neg1), 0u, L::SIGNREP)
+                               : spread<L>(h - v + L::MSB, sph, spl);
     const uint32_t vn = (h & M) | (v & ~M);
     h = h ^ v ^ vn;
     v = vn;
@@ -248,14 +286,15 @@ __device__ __forceinline__ void cell_mismatch(uint32_t &h, uint32_t &v, uint32_t
 // keys below half; rrv = rr per lane for full-width keys.
 template <class L>
 __device__ __forceinline__ uint32_t renorm_key(uint32_t k, uint32_t rr_bias, uint32_t rrv,
-                                               uint32_t one, uint32_t neg1)
+                                               uint32_t one, uint32_t neg1, uint32_t sph,
+                                               uint32_t spl)
 {
     if (L::FULL) {
         const uint32_t M = prmt(ge_lanes<L>(k, rrv, neg1), 0u, L::SIGNREP);
         return sub_lanes<L>(k, rrv) & M;
     }
     uint32_t t = mad_lo(k, one, rr_bias);     // lane: k + (half - rr), MSB iff k >= rr
-    uint32_t M = prmt(t, 0u, L::SIGNREP);
+    uint32_t M = spread<L>(t, sph, spl);
     return t & M & L::LOW;
 }
 
@@ -353,6 +392,28 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
             const uint32_t *sp = stage + j4 * (NGRP + 1) + grp;
             const uint32_t w0 = sp[0], w1 = sp[NGRP + 1], w2 = sp[2 * (NGRP + 1)], w3 = sp[3 * (NGRP + 1)];
             const int64_t off = i * p.ld + jbase + j4;
+            if (L::BITS == 10) {                // lanes are not byte-aligned: shift out
+                const uint32_t v0 = lane_of<L>(w0, b), v1 = lane_of<L>(w1, b);
+                const uint32_t v2 = lane_of<L>(w2, b), v3 = lane_of<L>(w3, b);
+                if (p.out_bytes == 1) {
+                    uint8_t *o = (uint8_t *)p.out + off;
+                    const uint32_t word = v0 | (v1 << 8) | (v2 << 16) | (v3 << 24);
+                    if (j4 + 4 <= cnt) {
+                        *(uint32_t *)o = word;
+                    } else {
+                        for (int t = 0; t < cnt - j4; ++t) o[t] = (uint8_t)(word >> (8 * t));
+                    }
+                } else {
+                    uint16_t *o = (uint16_t *)p.out + off;
+                    if (j4 + 4 <= cnt) {
+                        *(uint2 *)o = make_uint2(v0 | (v1 << 16), v2 | (v3 << 16));
+                    } else {
+                        const uint32_t v4[4] = {v0, v1, v2, v3};
+                        for (int t = 0; t < cnt - j4; ++t) o[t] = (uint16_t)v4[t];
+                    }
+                }
+                continue;
+            }
             // byte index of lane b's low byte inside a staged word
             const uint32_t bb = (uint32_t)(b * (L::BITS / 8));
             if (p.out_bytes == 1) {
@@ -516,9 +577,15 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
     const uint32_t one = p.one;
     const uint32_t neg1 = 0u - p.one;
     const uint32_t sh1 = p.shmul[1], sh2 = p.shmul[2], sh3 = p.shmul[3];
-    // multiplier of the byte shift for rows r = 1..RPW-1 past an aligned word
+    const uint32_t sl1 = p.shlo[1], sl2 = p.shlo[2], sl3 = p.shlo[3];
+    const uint32_t sph = p.spread_hi, spl = p.spread_lo;
+    // multipliers of the shift for rows r = 1..RPW-1 past an aligned word
+    // (16-bit lanes: r = 1 is a 2-byte shift)
     auto shm = [&](int r) -> uint32_t {
         return (L::BITS == 16) ? sh2 : (r == 1 ? sh1 : (r == 2 ? sh2 : sh3));
+    };
+    auto shl = [&](int r) -> uint32_t {
+        return (L::BITS == 16) ? sl2 : (r == 1 ? sl1 : (r == 2 ? sl2 : sl3));
     };
 
     int kc = wk;        // key of the first seaweed starting in this thread's unit
@@ -618,7 +685,7 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
             kc += SCORE ? 1 : 2;
             if (++since == p.renorm) {     // Proposition 3.4: old keys collapse to 0
 #pragma unroll
-                for (int k = 0; k < R; ++k) h[k] = renorm_key<L>(h[k], rr_bias, rrv, one, neg1);
+                for (int k = 0; k < R; ++k) h[k] = renorm_key<L>(h[k], rr_bias, rrv, one, neg1, sph, spl);
                 kc = wk;
                 since = 0;
             }
@@ -643,8 +710,8 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
             if (!XR) {
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
-                    mm0[q] = mismatch_mask<L, ST>(xw[q], yb0, one);
-                    mm1[q] = mismatch_mask<L, ST>(xw[q], yb1, one);
+                    mm0[q] = mismatch_mask<L, ST>(xw[q], yb0, one, sph, spl);
+                    mm1[q] = mismatch_mask<L, ST>(xw[q], yb1, one, sph, spl);
                 }
             }
 #pragma unroll
@@ -652,19 +719,19 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
                 const int q = k / L::RPW, r = k % L::RPW;
                 uint32_t m0, m1;
                 if (XR) {
-                    m0 = mismatch_mask<L, ST>(xw[k], yb0, one);
-                    m1 = mismatch_mask<L, ST>(xw[k], yb1, one);
+                    m0 = mismatch_mask<L, ST>(xw[k], yb0, one, sph, spl);
+                    m1 = mismatch_mask<L, ST>(xw[k], yb1, one, sph, spl);
                 } else {
-                    m0 = (r == 0) ? mm0[q] : row_shift(mm0[q], mm0[q + 1], shm(r));
-                    m1 = (r == 0) ? mm1[q] : row_shift(mm1[q], mm1[q + 1], shm(r));
+                    m0 = (r == 0) ? mm0[q] : row_shift(mm0[q], mm0[q + 1], shm(r), shl(r));
+                    m1 = (r == 0) ? mm1[q] : row_shift(mm1[q], mm1[q + 1], shm(r), shl(r));
                 }
                 const int pi = k - (R - PADU);
                 if (pi >= 0) {
                     m0 |= padm[pi < 0 ? 0 : pi];
                     m1 |= padm[pi < 0 ? 0 : pi];
                 }
-                cell<L>(h[k], va, m0, neg1);
-                cell<L>(h[k], vb, m1, neg1);
+                cell<L>(h[k], va, m0, neg1, sph, spl);
+                cell<L>(h[k], vb, m1, neg1, sph, spl);
             }
             vdown[0] = va;
             vdown[1] = vb;
@@ -687,15 +754,15 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
             uint32_t mm[XR ? 1 : NQ];
             if (!XR) {
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) mm[q] = mismatch_mask<L, ST>(xw[q], yb, one);
+                for (int q = 0; q < NQ; ++q) mm[q] = mismatch_mask<L, ST>(xw[q], yb, one, sph, spl);
             }
 #pragma unroll
             for (int q = 0; q < RP; ++q) {
                 const int pi = q - (RP - PADU);
                 const uint32_t pad = (pi >= 0) ? padm[pi < 0 ? 0 : pi] : 0u;
                 const int qq = q / L::RPW, r = q % L::RPW;
-                uint32_t mq = XR ? mismatch_mask<L, ST>(xw[q], yb, one)
-                                 : ((r == 0) ? mm[qq] : row_shift(mm[qq], mm[qq + 1], shm(r)));
+                uint32_t mq = XR ? mismatch_mask<L, ST>(xw[q], yb, one, sph, spl)
+                                 : ((r == 0) ? mm[qq] : row_shift(mm[qq], mm[qq + 1], shm(r), shl(r)));
                 if (pi >= 0) mq |= pad;
 #pragma unroll
                 for (int rho = 0; rho < NU; ++rho) {
@@ -705,16 +772,16 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
                         const bool row_dollar = rho < MU, col_dollar = c < MU;
                         if (row_dollar && col_dollar) {
                             if (pi >= 0) {
-                                cell<L>(h[k], v[c], pad, neg1);
+                                cell<L>(h[k], v[c], pad, neg1, sph, spl);
                             } else {
                                 const uint32_t tmp = h[k];
                                 h[k] = v[c];
                                 v[c] = tmp;
                             }
                         } else if (row_dollar != col_dollar) {
-                            cell_mismatch<L>(h[k], v[c], neg1);
+                            cell_mismatch<L>(h[k], v[c], neg1, sph, spl);
                         } else {
-                            cell<L>(h[k], v[c], mq, neg1);
+                            cell<L>(h[k], v[c], mq, neg1, sph, spl);
                         }
                     }
                 }

@@ -39,7 +39,8 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
 {
     const bool score = nu > 1;
     const int xrows = step > 1 ? 1 : 0;
-    // key_bits: 7 (w <= 120), 8 (LCS, w <= 254: values fit a byte), else 15.
+    // key_bits: 7 (w <= 120), 8 (LCS, w <= 254: values fit a byte), 9 (LCS, 10-bit
+    // lanes, 256 < w <= 480), else 15.
     int kbits = 0, rows = 0, groups = 0;
     auto rows_for = [&](int g, int unit, int lo, int hi) -> bool {
         // rows per thread for g threads: units (rows or pairs) rounded up to a
@@ -67,6 +68,15 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
         } else if (w <= 254) {
             kbits = 8;
             if (want_groups == 4 || !rows_for(2, 64, 64, 64)) rows_for(4, 4, 32, 64);
+        } else if (w > 256 && w <= 480) {
+            // 9-bit keys in 10-bit lanes, three strips per register.  Measured
+            // against 16-bit lanes on 100k DNA plots: w = 300: 536 vs 592 ms,
+            // w = 384: 701 vs 690 ms (16-bit lanes on 4 threads of 96 rows;
+            // on 8 threads, as built, 750 ms); at w = 256, where 16-bit lanes
+            // fit 4 threads of 64 rows exactly, 494 vs 472 ms, so w <= 256
+            // keeps 16-bit lanes.
+            kbits = 9;
+            if (want_groups == 8 || !rows_for(4, 3, 66, 96)) rows_for(8, 3, 33, 60);
         } else {
             kbits = 15;
             if (want_groups == 2 || want_groups == 4 || want_groups == 8)
@@ -127,11 +137,15 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
     } else if (v->key_bits == 8) {
         pl->ring = 256;
         pl->renorm = score ? (256 - w) : (256 - w) / 2;
+    } else if (v->key_bits == 9) {
+        // keys cycle through [w, 511]; exits are found by age, as for 15-bit keys
+        pl->ring = next_pow2(w + 1);
+        pl->renorm = (512 - w) / 2;
     } else {
         pl->ring = next_pow2(w + 1);
         pl->renorm = score ? (32768 - w) : (32768 - w) / 2;
     }
-    const int nlanes = v->lane_bits == 8 ? 4 : 2;
+    const int nlanes = v->lane_bits == 8 ? 4 : (v->lane_bits == 10 ? 3 : 2);
     pl->strips_per_warp = (32 / v->groups) * nlanes;
     const int ngrp = 32 / v->groups;
     pl->smem = (size_t)kWarpsPerBlock * (size_t)(pl->ring * ngrp + kOB * (ngrp + 1)) * 4u;
@@ -234,10 +248,22 @@ void fill_params(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y, 
                                  : ((a % 8 == 0) && (ld % 4 == 0));
     p->ring = pl.ring;
     p->one = 1u;
-    p->shmul[0] = 1u;
-    p->shmul[1] = 1u << 24;
-    p->shmul[2] = 1u << 16;
-    p->shmul[3] = 1u << 8;
+    if (pl.v->lane_bits == 10) {
+        // 10-bit lanes in bits 0-29: rows r = 1, 2 shift by 10r bits
+        p->shmul[0] = p->shlo[0] = 1u;
+        p->shmul[1] = 1u << 22;
+        p->shlo[1] = 1u << 20;
+        p->shmul[2] = 1u << 12;
+        p->shlo[2] = 1u << 10;
+        p->shmul[3] = p->shlo[3] = 0u;
+    } else {
+        p->shmul[0] = p->shlo[0] = 1u;
+        p->shmul[1] = p->shlo[1] = 1u << 24;
+        p->shmul[2] = p->shlo[2] = 1u << 16;
+        p->shmul[3] = p->shlo[3] = 1u << 8;
+    }
+    p->spread_hi = 1u << 23;
+    p->spread_lo = 0x3FFu;
     p->step = pl.step;
 }
 

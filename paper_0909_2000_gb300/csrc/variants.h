@@ -12,8 +12,8 @@ typedef void (*comb_fn_t)(CombParams);
 typedef void (*batch_fn_t)(BatchParams);
 
 struct Variant {
-    int key_bits;    // 7 (8-bit lanes), 8 (8-bit lanes, full keys) or 15 (16-bit lanes)
-    int lane_bits;   // 8 or 16
+    int key_bits;    // 7 (8-bit lanes), 8 (8-bit lanes, full keys), 9 (10-bit lanes) or 15
+    int lane_bits;   // 8, 10 or 16
     int rows;        // R: physical comb rows per thread
     int groups;      // G: threads per strip group
     int nu, mu;      // score blow-up {nu, mu, 0}; nu = 1 is LCS

@@ -60,6 +60,13 @@ CASES = [
     (600, 640, 200, b"AC", (2, 1, 0)),
     (600, 620, 254, b"ACGT", (2, 1, 0)),
     (620, 640, 255, b"ACGT", (2, 1, 0)),
+    # 10-bit lanes (three strips per register): 256 < w <= 480
+    (600, 620, 257, b"ACGT", (1, 0, 0)),
+    (700, 760, 300, b"ACGT", (1, 0, 0)),
+    (640, 700, 384, b"AC", (1, 0, 0)),
+    (600, 640, 480, b"ACGT", (1, 0, 0)),
+    (620, 600, 481, b"ACGT", (1, 0, 0)),
+    (560, 700, 299, bytes(range(256)), (1, 0, 0)),
     # the largest windows built: LCS w = 512 (16-bit lanes, 8 threads of 64
     # rows), {2,1,0} w = 256 (8 threads of 32 pairs)
     (700, 680, 512, b"ACGT", (1, 0, 0)),
