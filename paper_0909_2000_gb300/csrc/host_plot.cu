@@ -129,12 +129,14 @@ ap_status ap_alignment_plot_host(const uint8_t *x, int64_t m, const uint8_t *y, 
         tile_plan(&bp, br, pl.cols, 0, current_device());
         if (e == cudaSuccess)
             e = launch_comb(bp, dx + r0, m - r0, dy, n, buf, out_elem_bytes, L.band_ld, sk);
+        // the copy may start as soon as the band is combed: the dot kernels
+        // that follow on the compute stream only read the band
+        if (e == cudaSuccess) e = cudaEventRecord(combed[k], sk);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(copy, combed[k], 0);
         if (e == cudaSuccess && want_dots)      // dots in band order on the compute stream
             e = dots_pass(buf, out_elem_bytes, br, pl.cols, L.band_ld, threshold, r0, ddots,
                           dots_cap, (int32_t *)(ws + L.counts_off[k]),
                           (int64_t *)(ws + L.offsets_off[k]), running, sk);
-        if (e == cudaSuccess) e = cudaEventRecord(combed[k], sk);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(copy, combed[k], 0);
         char *dst = (char *)out + r0 * ld * out_elem_bytes;
         if (e == cudaSuccess && ld == L.band_ld)      // same row stride: one contiguous copy
             e = cudaMemcpyAsync(dst, buf, (size_t)(br * ld * out_elem_bytes), cudaMemcpyDeviceToHost,
