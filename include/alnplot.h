@@ -151,7 +151,8 @@ ap_status ap_set_lanes_per_strip(int32_t groups);
  * Errors: AP_E_INVAL for null pointers, w < 1, ld < cols, an element size
  * other than 1 or 2, or uint8 output when the largest possible value
  * (match * w) exceeds 255; AP_E_UNSUPPORTED for other
- * score schemes or w beyond the largest compiled comb height;
+ * score schemes or w beyond the largest compiled comb height (LCS w <= 512,
+ * {2,1,0} w <= 256);
  * AP_E_CUDA if a launch fails.  If m <= w or n <= w the plot is empty:
  * nothing is written and AP_OK is returned.  Stream-ordered; allocates no
  * device memory.
