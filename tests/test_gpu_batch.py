@@ -18,6 +18,7 @@ def dev(a):
 def make_jobs(seed=0):
     specs = [(1, (1, 0, 0)), (7, (1, 0, 0)), (16, (1, 0, 0)), (31, (1, 0, 0)), (64, (1, 0, 0)),
              (100, (1, 0, 0)), (120, (1, 0, 0)), (128, (1, 0, 0)), (200, (1, 0, 0)),
+             (300, (1, 0, 0)),
              (5, (2, 1, 0)), (64, (2, 1, 0)), (90, (2, 1, 0)), (130, (2, 1, 0))]
     jobs = []
     k = 0

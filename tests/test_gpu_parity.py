@@ -217,7 +217,8 @@ def test_plot_checksum_kernel(cuda_lib):
 
 
 @pytest.mark.parametrize("w,thr,scores", [(16, 11, (1, 0, 0)), (40, 29, (1, 0, 0)),
-                                          (24, 40, (2, 1, 0)), (130, 90, (1, 0, 0))])
+                                          (24, 40, (2, 1, 0)), (130, 90, (1, 0, 0)),
+                                          (300, 200, (1, 0, 0))])
 def test_dots_match_oracle(cuda_lib, w, thr, scores):
     ap = cuda_lib
     x = synth.dna(6, 1, 700)
