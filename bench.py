@@ -260,6 +260,10 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": "window-pair cells/sec (m*n*w/s)", "value": v,
         "unit": "cells/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        # one step is a bounded sample of the workload; the full plot would take
+        # m * n * w / value seconds
+        "ms_per_step": statistics.median([dt for _, _, dt in rates]) * 1e3,
+        "ms_per_full_workload": float(len(c.x)) * len(c.y) * c.w / v * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "config": describe(c),
         "cpu_baseline": {"value": v, "unit": "cells/s", "cores": cores(), "kind": "oracle",
