@@ -19,10 +19,12 @@
 //
 // GB300 mapping:
 //   * SWAR: one 32-bit register holds the same comb row of NS strips that
-//     are next to each other (4 x 8-bit keys, or 2 x 16-bit keys).  Strip
-//     i+b, row k reads x[i+b+k], so a row register is a 4-byte window of x.
-//     The match mask of each aligned x word is computed once per column,
-//     and the rows are byte shifts (PRMT) of those masks.
+//     are next to each other (4 x 8-bit lanes, 3 x 10-bit lanes or 2 x
+//     16-bit lanes).  Strip i+b, row k reads x[i+b+k], so a row register is
+//     an NS-character window of x.  The match mask of each aligned x word is
+//     computed once per column, and the other rows' masks are lane shifts of
+//     those masks, done as multiplies on the FMA pipe (the cells keep the
+//     ALU pipe busy).
 //   * Keys are start columns, not distances, so columns need no increment.
 //     Every Rr columns all keys drop by Rr, saturating at 0 (0 = "older
 //     than any window").  The new seaweed's key cycles in [w, KMAX].
@@ -37,7 +39,10 @@
 //   * When a strip's rows are split over G lanes, the wavefront is skewed
 //     by one column per lane, and v passes down with a warp shuffle.
 //   * Results are staged in shared memory and written to HBM as
-//     row-contiguous, sector-aligned stores.
+//     row-contiguous, sector-aligned stores (16 bytes per thread where the
+//     rows allow).
+//   * Tiles whose characters all share the top bit take a shorter mismatch
+//     test (one logic instruction fewer per x word).
 //
 // Score mode ({2,1,0}, Section 2): the comb runs on the '$'-interleaved
 // strings x' = $x0$x1..., y' = $y0$y1...  Rows and columns alternate '$'
