@@ -118,11 +118,22 @@ ap_status ap_alignment_plot_host(const uint8_t *x, int64_t m, const uint8_t *y, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, (size_t)m, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, (size_t)n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && want_dots) e = cudaMemsetAsync(running, 0, sizeof(int64_t), st);
+    // Band sizes: full bands, then halving ones (down to a quarter band) over
+    // the last two bands' worth of rows, so that the copy of the final band,
+    // which nothing overlaps, is short.  Whole strip groups per band.
+    const int64_t spw = pl.strips_per_warp;
+    const int64_t quarter = std::max<int64_t>(spw, L.band_rows / 4 / spw * spw);
+    auto next_band = [&](int64_t left) -> int64_t {
+        int64_t half = (left + 1) / 2;
+        half = (half + spw - 1) / spw * spw;
+        return std::min(left, std::min(L.band_rows, std::max(quarter, half)));
+    };
     int band = 0;
-    for (int64_t r0 = 0; r0 < pl.rows && e == cudaSuccess; r0 += L.band_rows, ++band) {
+    int64_t br = 0;
+    for (int64_t r0 = 0; r0 < pl.rows && e == cudaSuccess; r0 += br, ++band) {
         const int k = band & 1;
         cudaStream_t sk = cs[k];
-        const int64_t br = std::min(L.band_rows, pl.rows - r0);
+        br = next_band(pl.rows - r0);
         void *buf = ws + L.buf_off[k];
         if (band >= 2) e = cudaStreamWaitEvent(sk, copied[k], 0);   // buffer k is free again
         Plan bp = pl;
