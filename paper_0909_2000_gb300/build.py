@@ -10,6 +10,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import hashlib
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -138,11 +139,20 @@ def _deps_digest() -> str:
     return h.hexdigest()
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and blank lines: what the compiler sees
+    (string literals in comb.cuh hold no comment markers)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def kernel_digest() -> str:
-    """Digest of the strip-comb kernel source and variant list (used to tell
-    whether stored profiler counters still describe the current kernel)."""
+    """Digest of the strip-comb kernel code (comments left out) and variant
+    list, used to tell whether stored profiler counters still describe the
+    current kernel."""
     h = hashlib.sha1()
-    h.update(open(os.path.join(CSRC, "comb.cuh"), "rb").read())
+    h.update(_code_only(open(os.path.join(CSRC, "comb.cuh")).read()).encode())
     h.update(repr(VARIANTS).encode())
     return h.hexdigest()[:16]
 

@@ -470,7 +470,7 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
 // The kernel
 // ---------------------------------------------------------------------------
 //
-// L      lane format (U8Lanes / U16Lanes)
+// L      lane format (U8Lanes, U8FLanes, U10Lanes or U16Lanes)
 // R      physical comb rows held by each thread
 // G      threads per strip group (the strip's rows are split over them)
 // NU, MU blow-up of the score scheme {NU, MU, 0}: every character becomes
@@ -481,7 +481,9 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
 // XR     vertical step: plot row r is the x-window at r * step, so the NS
 //        strips of a register are not neighbours; each thread then keeps one
 //        x word per unit (gathered once per tile) and computes each unit's
-//        match mask directly instead of byte-shifting shared masks
+//        match mask directly instead of lane-shifting shared masks
+// ST     every character this tile compares shares the top bit: the short
+//        mismatch test is exact (chosen per tile by comb_tile_dispatch)
 //
 // Each step combs two physical columns, interleaved row by row, so a thread
 // always has two independent dependency chains:
