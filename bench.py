@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=None,
+                    help="seconds of oracle work per reference-arm step (default: "
+                         "150 s over all steps, 2..10 s each)")
     return ap.parse_args()
 
 
@@ -250,7 +253,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     c = workload(args.workload)
-    per = max(2.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    per = args.ref_seconds or max(2.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
     rates = []
     for s in range(args.warmup + args.steps):
         r, k, dt, nth = oracle_rate(c, per, seed=100 + s)

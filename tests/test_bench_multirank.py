@@ -44,3 +44,27 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(12.5) == 12.5
     assert bench.weak_scaling_value(10.0, 1, 2, 1000.0) == 20.0
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference (the CPU oracle, no GPU) prints one JSON line
+    with the contract's keys, its own cpu_baseline and a zero-copy e2e."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--workload", "lcs_dna_512_w16", "--steps", "2", "--warmup", "1",
+                        "--ref-seconds", "0.5"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
+    assert d["config"]["workload"] == "lcs_dna_512_w16"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
