@@ -14,6 +14,19 @@ roofline: the strip-comb kernel is bound by the integer ALU.  Its algorithmic
     register.  Comb cells per plot = (m - w)(n - 1)w.  The peak is
     SMs x 32-bit integer lanes per SM per clock x the SM clock.
 
+After the headline, the default run (one GPU) adds a record for each other
+workload, under "workloads", each with its own clock record and parity flag:
+    lcs_dna_512_w16        LCS, DNA m = n = 512, w = 16: time per call, full
+                           plot against the oracle;
+    score_protein_20k_w64  {2,1,0}, 20-letter protein m = n = 20,000, w = 64,
+                           uint16 plot: cells/s, roofline, whole-plot digest
+                           against the stored oracle digest, oracle samples;
+    batch_dna_4096         4096 DNA pairs as one graph launch against a loop of
+                           plain calls: both times, identical outputs, samples;
+    serve_dna_poisson      Poisson arrivals into the server: capacity under the
+                           offered 200 req/s, p50/p99 at 70% of capacity,
+                           served dots against plain calls and the oracle.
+
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank combs its own copy of the workload (independent
 problems, no collective on the data path; weak scaling).
@@ -54,6 +67,10 @@ def parse_args():
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the records of the other workloads in the default run")
+    ap.add_argument("--workloads-steps", type=int, default=3,
+                    help="timed steps of each other workload's record (default 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=None,
@@ -246,6 +263,137 @@ def profile_traffic(kernel_tag):
     return None
 
 
+def read_golden(name):
+    """Stored digest of a workload's whole plot (tests/golden/<name>.txt,
+    written from the oracle by tests/golden/make_golden.py), or None."""
+    path = os.path.join(ROOT, "tests", "golden", name + ".txt")
+    try:
+        kv = dict(line.split("=", 1) for line in open(path).read().split() if "=" in line)
+    except OSError:
+        return None
+    return {"checksum": int(kv["checksum"]), "histogram": [int(v) for v in kv["histogram"].split(",")],
+            "shape": tuple(int(v) for v in kv["shape"].split("x"))}
+
+
+def golden_check(ap, plot, name, nbins):
+    """The GPU checksum kernel's digest of `plot` against the stored oracle
+    digest: True / False, or None when no digest is stored."""
+    g = read_golden(name)
+    if g is None:
+        return None
+    cs, hist = ap.plot_checksum(plot, nbins)
+    return bool(tuple(plot.shape) == g["shape"] and cs == g["checksum"] and list(hist) == g["histogram"])
+
+
+def event_times(fn, steps, stream, flush=None):
+    """CUDA-event milliseconds of `steps` calls of fn on `stream`, each
+    bracketed by synchronisations, with an optional L2 flush before each."""
+    import torch
+    ms = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def comb_roofline(plan, rows, n, w, score, comb_ms, sms, clk):
+    """Integer-issue roofline of one comb launch: algorithmic 32-bit ops =
+    comb cells x 6 lane-ops / lanes per register, over the launch time."""
+    comb_cells = float(rows) * (n - 1) * (2 * w if score else w) * (2 if score else 1)
+    alg_ops = comb_cells * LANE_OPS_PER_CELL / plan["strips_per_reg"]
+    achieved = alg_ops / (comb_ms / 1e3) / 1e12
+    peak = sms * INT32_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "ops_per_cell": LANE_OPS_PER_CELL / plan["strips_per_reg"], "comb_ms": comb_ms,
+            "peak_basis": "%d SMs x %d int32 lanes/clk x %.0f MHz (max SM clock)"
+                          % (sms, INT32_LANES_PER_SM_CLK, SM_MAX_MHZ),
+            "frac_at_measured_clock": (achieved / (sms * INT32_LANES_PER_SM_CLK * clk["sm_mhz"] * 1e6 / 1e12)
+                                       if clk else None)}
+
+
+def percentiles(ms):
+    v = sorted(ms)
+
+    def pct(p):
+        return v[min(len(v) - 1, max(0, int(math.ceil(p * len(v))) - 1))]
+    return {"p10": pct(0.10), "p50": pct(0.50), "p90": pct(0.90), "min": v[0], "max": v[-1]}
+
+
+# ---------------------------------------------------------------------------
+# Records of the other workloads, run after the headline in the default run
+# (one GPU), each with its own clock record and parity flag
+# ---------------------------------------------------------------------------
+
+def plot_record(ap, c, steps, warmup, dev, host_calls=0):
+    """One plot workload: comb time per call (CUDA events, L2 flushed before
+    each), cells/s, the integer roofline, and parity: the whole plot against
+    the oracle where it is small, else the stored whole-plot digest plus
+    seeded oracle samples."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_0909_2000_gb300 import synth
+    m, n, w = len(c.x), len(c.y), c.w
+    score = tuple(c.scores[:2]) == (2, 1)
+    scores = ap.SCORE if score else ap.LCS
+    rows, cols = ap.plot_shape(m, n, w)
+    plan = ap.plot_plan(m, n, w, scores)
+    x, y = torch.from_numpy(c.x).to(dev), torch.from_numpy(c.y).to(dev)
+    out = ap.empty_plot(rows, cols, torch.int16 if wide(c) else torch.uint8, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def call():
+        ap.alignment_plot(x, y, w, scores, out=out)
+    for _ in range(warmup):
+        call()
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    ms = event_times(call, steps, stream, flush)
+    host_ms = None
+    if host_calls:
+        # back-to-back calls with no synchronisation between them: what one
+        # call costs a caller when the plot is too small to hide the launch
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(host_calls):
+            call()
+        torch.cuda.synchronize()
+        host_ms = (time.perf_counter() - t0) * 1e3 / host_calls
+    clk = clocks.stop()
+    props = torch.cuda.get_device_properties(dev)
+    comb_ms = statistics.mean(ms)
+    rec = {"workload": c.name, "m": m, "n": n, "w": w, "scores": "{%d,%d,0}" % tuple(c.scores[:2]),
+           "output": "%dx%d %s" % (rows, cols, "uint16" if wide(c) else "uint8"), "steps": steps,
+           "ms_per_call": statistics.median(ms), "ms_spread": percentiles(ms),
+           "value": float(m) * n * w / (statistics.median(ms) / 1e3), "unit": "cells/s",
+           "roofline": comb_roofline(plan, rows, n, w, score, comb_ms, props.multi_processor_count, clk),
+           "plan": plan, "clocks": clk}
+    if host_ms is not None:
+        rec["host_ms_per_call_back_to_back"] = host_ms
+        rec["host_calls"] = host_calls
+    if rows * cols <= 1 << 20:
+        got = out.cpu().numpy().astype(np.int64) & 0xFFFF
+        rec["parity"] = {"oracle_full_plot_equal": bool(np.array_equal(got, oracle.plot(c.x, c.y, w, *c.scores[:2])))}
+    else:
+        ii, jj = synth.below(13, 1, 2000, rows), synth.below(13, 2, 2000, cols)
+        got = out[torch.from_numpy(ii).to(dev), torch.from_numpy(jj).to(dev)].cpu().numpy().astype(np.int64) & 0xFFFF
+        rec["parity"] = {"oracle_samples_ok": bool(np.array_equal(got, oracle.samples(c.x, c.y, w, ii, jj, *c.scores[:2]))),
+                         "oracle_samples": 2000,
+                         "golden_digest_ok": golden_check(ap, out, c.name, c.scores[0] * w + 1)}
+    del out, flush
+    torch.cuda.empty_cache()
+    return rec
+
+
 # ---------------------------------------------------------------------------
 
 def run_reference(args):
@@ -279,7 +427,7 @@ def run_reference(args):
     return 0
 
 
-def bench_batch(args):
+def batch_record(args, steps, warmup):
     """Many DNA pairs (lengths log-uniform 200..20000, w in {16,32,64,128},
     30% with a planted homology): one batched graph launch per step, against a
     loop of plain calls (one launch per pair) on the same GPU, same outputs."""
@@ -287,6 +435,7 @@ def bench_batch(args):
     import numpy as np
     import torch
 
+    import oracle
     import paper_0909_2000_gb300 as ap
     from paper_0909_2000_gb300 import synth
 
@@ -336,33 +485,20 @@ def bench_batch(args):
                      autotune=True)
     create_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
-
-    def timed(fn, steps):
-        ms = []
-        for _ in range(steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        return ms
-
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plain()
         batch.run()
     torch.cuda.synchronize()
     clocks = Clocks(0)
     clocks.start()
-    ms_p = timed(plain, args.steps)
-    ms_b = timed(batch.run, args.steps)
+    # the outputs (73.5 GB) are far larger than L2: no flush is needed
+    ms_p = event_times(plain, steps, stream)
+    ms_b = event_times(batch.run, steps, stream)
     clk = clocks.stop()
     same = bool(torch.equal(OUT_P, OUT_B))
     # oracle spot checks on seeded (job, i, j) samples
-    import oracle
     rng = synth.below(5, 1, 300, len(jobs))
-    ok = True
+    ok, nsamp = True, 0
     for t, k in enumerate(rng):
         r, c, _ = shapes[k]
         if r == 0 or c == 0:
@@ -371,26 +507,42 @@ def bench_batch(args):
         jj = synth.below(5, 20000 + t, 4, c)
         got = outs_b[k][torch.from_numpy(ii).to(dev), torch.from_numpy(jj).to(dev)].cpu().numpy()
         ok &= bool(np.array_equal(got.astype(np.int64), oracle.samples(jobs[k].x, jobs[k].y, jobs[k].w, ii, jj)))
+        nsamp += 4
     info = batch.info()
+    batch.close()
     tb, tp = statistics.median(ms_b) / 1e3, statistics.median(ms_p) / 1e3
-    line = {
-        "metric": "window-pair cells/sec (m*n*w/s)", "value": logical / tb, "unit": "cells/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tb * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic",
-        "config": {"workload": "batch_dna_%d" % len(jobs),
-                   "jobs": "%d DNA pairs, m and n log-uniform 200..20000, w uniform in {16,32,64,128}, "
-                           "30%% with one planted homology (length min(m,n)/4, 10%% substitutions)" % len(jobs),
-                   "output": "every pair's full uint8 plot (%.1f GB)" % (oo[-1] / 1e9)},
-        "batched": {"ms": tb * 1e3, "cells_per_s": logical / tb, "info": info, "create_s": create_s},
-        "plain_loop": {"ms": tp * 1e3, "cells_per_s": logical / tp,
-                       "note": "one ap_alignment_plot call per pair, same stream"},
+    rec = {
+        "workload": "batch_dna_%d" % len(jobs),
+        "jobs": "%d DNA pairs, m and n log-uniform 200..20000, w uniform in {16,32,64,128}, "
+                "30%% with one planted homology (length min(m,n)/4, 10%% substitutions)" % len(jobs),
+        "output": "every pair's full uint8 plot (%.1f GB)" % (oo[-1] / 1e9), "steps": steps,
+        "value": logical / tb, "unit": "cells/s",
+        "batched": {"ms": tb * 1e3, "ms_spread": percentiles(ms_b), "cells_per_s": logical / tb, "info": info,
+                    "create_s": create_s, "gpu_launches_per_step": 1},
+        "plain_loop": {"ms": tp * 1e3, "ms_spread": percentiles(ms_p), "cells_per_s": logical / tp,
+                       "note": "one ap_alignment_plot call per pair, same stream",
+                       "gpu_launches_per_step": sum(1 for r, c, _ in shapes if r and c)},
         "speedup_batched_vs_plain": tp / tb,
-        "outputs_identical": same, "oracle_samples_ok": ok, "clocks": clk, "gen_s": gen_s,
-        "gpu_launches": 1,
+        "parity": {"outputs_identical_to_plain": same, "oracle_samples_ok": ok, "oracle_samples": nsamp},
+        "clocks": clk, "gen_s": gen_s,
     }
+    del OUT_P, OUT_B, X, Y, outs_p, outs_b, xs, ys
+    torch.cuda.empty_cache()
+    return rec
+
+
+def bench_batch(args):
+    rec = batch_record(args, args.steps, args.warmup)
+    line = {"metric": "window-pair cells/sec (m*n*w/s)", "value": rec["value"], "unit": "cells/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["batched"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": rec["workload"], "jobs": rec["jobs"],
+                                            "output": rec["output"]},
+            "gpu_launches": args.steps}
+    line.update({k: rec[k] for k in ("batched", "plain_loop", "speedup_batched_vs_plain", "parity", "clocks")})
     print(json.dumps(line), flush=True)
-    return 0 if (same and ok) else 1
+    p = rec["parity"]
+    return 0 if (p["outputs_identical_to_plain"] and p["oracle_samples_ok"]) else 1
 
 
 def bench_table1_shape(args):
@@ -408,8 +560,8 @@ def bench_table1_shape(args):
 
     ap.load(build_if_missing=True)
     dev = torch.device("cuda", 0)
-    c = synth.dna_plot_100k(0, m=80_000, n=80_000, w=100, segments=16, seg_len=2000)
-    step = 5
+    c = synth.dna_score_80k_step5(0)
+    step = c.step
     x = torch.from_numpy(c.x).to(dev)
     y = torch.from_numpy(c.y).to(dev)
     rows = -(-(len(c.x) - c.w) // step)
@@ -440,21 +592,26 @@ def bench_table1_shape(args):
                        "step": step, "scores": "match 2, mismatch 1, gap 0 (the paper's 1, 0, -1/2)",
                        "output": "%d x %d uint8 plot" % (rows, cols)},
             "paper_table1_same_shape_s": {"sea8_1core_core2_1.83GHz": 1614, "mpi_64cores_xeon_3GHz": 23},
-            "seconds": t, "oracle_samples_ok": bool(np.array_equal(got, want))}
+            "seconds": t, "oracle_samples_ok": bool(np.array_equal(got, want)),
+            "golden_digest_ok": golden_check(ap, out, c.name, 2 * c.w + 1)}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def bench_serve(args):
+def serve_record(args, overload_seconds, sustained_seconds, check_requests=12, plain_requests=60):
     """Open-loop Poisson arrivals of DNA dot-plot requests (m, n log-uniform
     1000..200000, w uniform in {32,64,128,256}, dots >= ceil(0.8 w)) into the
-    server; p50/p99 latency, throughput, offered load; then the same at a rate
-    the GPU sustains; and a loop of plain dots calls for comparison."""
+    server: first at the offered rate (args.serve_rate) for overload_seconds,
+    whose throughput under the backlog is the capacity; then at 70% of that
+    capacity for sustained_seconds, with p50/p99 latency; served dots of
+    seeded requests against plain calls and the oracle; and a sequential loop
+    of plain dots calls on the same kind of requests for comparison."""
     import threading as th
 
     import numpy as np
     import torch
 
+    import oracle
     import paper_0909_2000_gb300 as ap
     from paper_0909_2000_gb300 import synth
 
@@ -470,7 +627,8 @@ def bench_serve(args):
         tickets = [None] * len(reqs)
         # a seeded set of moderate requests whose dots are kept for checking
         small = [k for k, (_, p) in enumerate(reqs) if cells(p) < 5e11]
-        keep = set(small[int(i)] for i in synth.below(seed, 77, 12, len(small))) if (check is not None and small) else set()
+        keep = (set(small[int(i)] for i in synth.below(seed, 77, check_requests, len(small)))
+                if (check is not None and small) else set())
         t0 = time.perf_counter()
 
         def submitter():
@@ -504,16 +662,15 @@ def bench_serve(args):
 
     clocks = Clocks(0)
     clocks.start()
-    overload = run(args.serve_rate, args.serve_seconds, 0)
+    overload = run(args.serve_rate, overload_seconds, 0)
     capacity = overload["throughput_cells_per_s"]
     sust_rate = max(1.0, 0.7 * capacity / overload["mean_cells_per_request"])
     checked = []
-    sustained = run(sust_rate, max(10.0, args.serve_seconds), 1, checked)
+    sustained = run(sust_rate, sustained_seconds, 1, checked)
     clk = clocks.stop()
     # served dots against the plain call and the oracle (outside the timing):
     # identical dot lists, every sampled dot's value, and sampled non-dots
     # below the threshold
-    import oracle
     dev = torch.device("cuda", 0)
     same, oracle_ok, nsamp = True, True, 0
     for k, (p, dots) in enumerate(checked):
@@ -538,7 +695,7 @@ def bench_serve(args):
             oracle_ok &= bool((v < p.threshold).all())
             nsamp += len(off)
     # plain form: the same kind of requests, one ap_alignment_dots call after another
-    reqs = synth.serving_requests(2, rate=args.serve_rate, duration=1.0)[:60]
+    reqs = synth.serving_requests(2, rate=args.serve_rate, duration=1.0)[:plain_requests]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _, p in reqs:
@@ -548,23 +705,30 @@ def bench_serve(args):
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t0
     plain_rate = sum(cells(p) for _, p in reqs) / plain_s
-    line = {
-        "metric": "window-pair cells/sec (m*n*w/s)", "value": sustained["throughput_cells_per_s"],
-        "unit": "cells/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8/u16 keys", "data": "synthetic",
-        "config": {"workload": "serve_dna_poisson",
-                   "requests": "Poisson arrivals; m, n log-uniform 1000..200000; w uniform in "
-                               "{32,64,128,256}; dots >= ceil(0.8 w); device budget 64 GiB, %d slots"
-                               % args.serve_slots},
+    return {
+        "workload": "serve_dna_poisson",
+        "requests": "Poisson arrivals; m, n log-uniform 1000..200000; w uniform in {32,64,128,256}; "
+                    "dots >= ceil(0.8 w); device budget 64 GiB, %d slots" % args.serve_slots,
+        "value": sustained["throughput_cells_per_s"], "unit": "cells/s",
+        "capacity_cells_per_s": capacity,
         "open_loop_at_offered_rate": overload,
         "open_loop_at_sustainable_rate": sustained,
         "offered_over_capacity": overload["offered_cells_per_s"] / capacity,
         "plain_sequential_dots": {"requests": len(reqs), "cells_per_s": plain_rate},
-        "served_over_plain": capacity / plain_rate,
+        "served_capacity_over_plain": capacity / plain_rate,
         "parity": {"requests_checked": len(checked), "identical_to_plain_calls": same,
                    "oracle_samples_ok": oracle_ok, "oracle_samples": nsamp},
         "clocks": clk,
     }
+
+
+def bench_serve(args):
+    rec = serve_record(args, args.serve_seconds, max(10.0, args.serve_seconds))
+    line = {"metric": "window-pair cells/sec (m*n*w/s)", "value": rec["value"], "unit": "cells/s",
+            "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8/u16 keys", "data": "synthetic",
+            "config": {"workload": rec["workload"], "requests": rec["requests"]}}
+    line.update({k: v for k, v in rec.items() if k not in ("workload", "requests", "value", "unit")})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -671,6 +835,9 @@ def main():
         out[torch.from_numpy(ii).to(dev), torch.from_numpy(jj).to(dev)].cpu().numpy().astype(np.int64)
     want = oracle.samples(c.x, c.y, w, ii, jj, c.scores[0], c.scores[1])
     parity_ok = bool(np.array_equal(got, want))
+    # the whole plot's digest against the oracle's stored digest
+    golden_ok = golden_check(ap, out, c.name, c.scores[0] * w + 1)
+    dev_dots = ap.dots_to_numpy(dots, ndots) if thr is not None else None
 
     # roofline of the comb kernel (integer ALU)
     comb_cells = float(rows) * (n - 1) * (2 * w if score else w) * (2 if score else 1)
@@ -683,9 +850,11 @@ def main():
     peak = sms * INT32_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     traffic = profile_traffic("comb/" + c.name)
 
+    del out, ws, flush
+    torch.cuda.empty_cache()
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(ap, c, scores, thr, dev, min(args.steps, 5), dist, world)
+        e2e = measure_e2e(ap, c, scores, thr, dev, max(5, min(args.steps, 10)), dist, world, dev_dots)
 
     line = {
         "metric": "window-pair cells/sec (m*n*w/s)",
@@ -708,6 +877,7 @@ def main():
         "physical_cells_per_s": plan["physical_cells"] / comb_s,
         "dots": ndots,
         "parity_samples_ok": parity_ok,
+        "parity": {"oracle_samples_ok": parity_ok, "oracle_samples": 2000, "golden_digest_ok": golden_ok},
         "clocks": clk,
         "wall_s": wall,
     }
@@ -719,6 +889,18 @@ def main():
                                 "cpu": cpu_model(),
                                 "sample": "%d seeded window pairs of this workload, O(w^2) DP each, "
                                           "%.1f s on %d host threads" % (k, dt, nth)}
+    if world == 1 and not args.no_workloads and args.workload == "lcs_dna_100k_w100":
+        # the other workloads, each on its own after the headline's timing
+        from paper_0909_2000_gb300 import synth
+        k = max(1, args.workloads_steps)
+        others = {}
+        t0 = time.perf_counter()
+        others["lcs_dna_512_w16"] = plot_record(ap, synth.dna_plot_512(0), max(k, 20), 3, dev, host_calls=2000)
+        others["score_protein_20k_w64"] = plot_record(ap, synth.protein_score_20k(0), max(k, 10), 3, dev)
+        others["batch_dna_4096"] = batch_record(args, k, 1)
+        others["serve_dna_poisson"] = serve_record(args, 4.0, 20.0)
+        line["workloads"] = others
+        line["workloads_wall_s"] = time.perf_counter() - t0
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -726,14 +908,20 @@ def main():
     return 0
 
 
-def measure_e2e(ap, c, scores, thr, dev, steps, dist=None, world=1):
+def measure_e2e(ap, c, scores, thr, dev, steps, dist=None, world=1, dev_dots=None):
     """Same metric through the public API from and to host memory:
     ap_alignment_plot_host copies x, y in from pinned host memory, combs the
     plot band by band and copies every band (and the dots) back while the
     next band is combed.  Timed per call, every byte moved inside.  Under
     torchrun every rank runs its own calls between barriers; the step time
-    is the slowest rank's and the value counts all ranks' cells."""
+    is the slowest rank's and the value counts all ranks' cells.  After the
+    timing, the host plot of the last call is checked against the oracle on
+    seeded samples, and its dots against the device path's dots."""
+    import numpy as np
     import torch
+
+    import oracle
+    from paper_0909_2000_gb300 import synth
     m, n, w = len(c.x), len(c.y), c.w
     rows, cols = ap.plot_shape(m, n, w)
     dt = torch.int16 if wide(c) else torch.uint8
@@ -758,10 +946,17 @@ def measure_e2e(ap, c, scores, thr, dev, steps, dist=None, world=1):
         out, dots, count = ap.alignment_plot_host(hx, hy, w, scores, out=hout, threshold=thr)
         ts.append(max_over_ranks((time.perf_counter() - t0) * 1e3, dist, dev) / 1e3)
     t = statistics.median(ts)
+    ii, jj = synth.below(17, 1, 2000, rows), synth.below(17, 2, 2000, cols)
+    got = hout.numpy()[ii, jj].astype(np.int64) & 0xFFFF
+    parity = {"host_plot_oracle_samples_ok": bool(np.array_equal(got, oracle.samples(c.x, c.y, w, ii, jj,
+                                                                                      *c.scores[:2]))),
+              "oracle_samples": 2000}
+    if thr is not None and dev_dots is not None:
+        parity["host_dots_equal_device_dots"] = bool(count == len(dev_dots) and np.array_equal(dots, dev_dots))
     return {"value": float(m) * n * w * world / t, "unit": "cells/s", "h2d_bytes_per_step": (m + n) * world,
             "d2h_bytes_per_step": (rows * ld * hout.element_size() + (count or 0) * 12 + 8) * world,
-            "ms_per_step": t * 1e3, "steps": steps,
-            "api": "ap_alignment_plot_host (band copies overlap the comb)"}
+            "ms_per_step": t * 1e3, "steps": steps, "ms_spread": percentiles([v * 1e3 for v in ts]),
+            "parity": parity, "api": "ap_alignment_plot_host (band copies overlap the comb)"}
 
 
 if __name__ == "__main__":

@@ -129,6 +129,19 @@ ap_status ap_plot_plan(int64_t m, int64_t n, int32_t w,
 ap_status ap_set_chunk(int64_t chunk);
 
 /*
+ * Tuning and testing: force the band height of the banded calls, which comb
+ * a plot a band of rows at a time into device memory (ap_alignment_dots,
+ * ap_alignment_plot_host, and the jobs that ap_server_submit plans), to
+ * `rows` plot rows rounded up to whole strip groups; 0 restores the
+ * automatic choice (about 1 GB of plot per band).  Each band combs its rows
+ * exactly as one call would (strips are independent, Theorem 3.1), so
+ * results do not depend on it; small bands make small plots take the
+ * many-band path.  A workspace size queried under one setting serves calls
+ * under the same setting.  Process-wide; AP_E_INVAL if rows < 0.
+ */
+ap_status ap_set_band_rows(int64_t rows);
+
+/*
  * Tuning: ask for `groups` threads per group of strips (the comb rows of one
  * strip are split over them; 0 restores the automatic choice).  Honoured
  * when a compiled variant exists for the window length, else the automatic
@@ -265,12 +278,16 @@ ap_status ap_plot_dots(const void *plot, int32_t elem_bytes, int64_t rows,
  * 3 MiB), and every GPU that loads the library holds it until the process
  * exits.  Taller plots are rejected with AP_E_NOMEM.
  *
- * The first call on a device looks up the array's address on that device
- * (the device current at the call); make that first call before any stream
- * capture.  All calls share the one array, which keeps the last call's
- * contents.  Each call clears what must start at zero, but calls whose GPU
- * work overlaps (different streams or host threads) race on the array, so
- * the caller must order them.
+ * Every call looks up the array's address on the device current at the
+ * call.  The first call in a process on a device also loads the library's
+ * module holding the array there, which takes those ~3 MiB of device memory
+ * at that moment (and can fail with AP_E_CUDA if the device is full).  So
+ * make one call per device at start-up, before any stream capture and
+ * before the host program takes the rest of the memory: a call with
+ * rows = 0 (plot may then be null) does only that.  All calls share the
+ * one array, which keeps the last call's contents.  Each call clears what
+ * must start at zero, but calls whose GPU work overlaps (different streams
+ * or host threads) race on the array, so the caller must order them.
  *
  * Arguments, results, dot order and the overflow rule are those of
  * ap_plot_dots.  Synchronises `stream` before returning.

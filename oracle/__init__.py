@@ -22,6 +22,14 @@ efficiently", Section 2.
 
 ``oracle.c`` holds the same recurrence as compiled C, threaded over plot rows
 or samples.  The pure-Python functions below restate it for small cases.
+
+``blcs.c`` is a second reference for plots too large for the dynamic
+programme: the bit-parallel LCS of Crochemore et al. (2001), the comparison
+method of the paper's Section 4, run once per window pair, with scores
+{nu, mu, 0} through the blow-up of Section 2.  It is trusted only through
+the tests that check it against the dynamic programme and the brute-force
+pins.  Both report plot digests (checksum and value histogram) for whole
+plots without storing them.
 """
 from __future__ import annotations
 
@@ -33,7 +41,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "blcs.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -46,11 +54,11 @@ def build(force: bool = False) -> str:
     """Compile ``oracle.c`` into ``liboracle.so`` next to it with gcc."""
     with _lock:
         fresh = (os.path.exists(_LIB_PATH)
-                 and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC))
+                 and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS))
         if force or not fresh:
             tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
             subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
-                                   "-pthread", _SRC, "-o", tmp])
+                                   "-pthread"] + _SRCS + ["-o", tmp])
             os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -69,6 +77,15 @@ def _load():
         lib.oracle_samples.restype = ctypes.c_int
         lib.oracle_samples.argtypes = [p, i64, p, i64, i64, i32, i32, p, p,
                                        i64, p, ctypes.c_int]
+        lib.oracle_plot_digest.restype = ctypes.c_int
+        lib.oracle_plot_digest.argtypes = [p, i64, p, i64, i64, i32, i32, i64, i32, p,
+                                           ctypes.c_int]
+        lib.oracle_blcs_plot.restype = ctypes.c_int
+        lib.oracle_blcs_plot.argtypes = [p, i64, p, i64, i64, i32, i32, i64, p, i64,
+                                         ctypes.c_int]
+        lib.oracle_blcs_digest.restype = ctypes.c_int
+        lib.oracle_blcs_digest.argtypes = [p, i64, p, i64, i64, i32, i32, i64, i32, p,
+                                           ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -132,6 +149,62 @@ def samples(x, y, w: int, ii, jj, match: int = 1, mismatch: int = 0,
         if rc != 0:
             raise ValueError("oracle_samples: index outside the plot")
     return out
+
+
+def step_shape(m: int, n: int, w: int, step: int) -> tuple[int, int]:
+    """Shape of the plot of every step-th x-window (Section 3's step h)."""
+    return (-(-(m - w) // step) if m > w else 0), max(0, n - w)
+
+
+def plot_digest(x, y, w: int, match: int = 1, mismatch: int = 0, step: int = 1,
+                nbins: int | None = None, nthreads: int | None = None):
+    """(checksum, histogram) of the whole plot by the dynamic programme, row r
+    being the x-window at r * step, without storing the plot.  nbins defaults
+    to match * w + 1 (every possible value)."""
+    x, y = _u8(x), _u8(y)
+    nbins = match * w + 1 if nbins is None else nbins
+    res = np.zeros(1 + nbins, dtype=np.uint64)
+    rc = _load().oracle_plot_digest(x.ctypes.data, len(x), y.ctypes.data, len(y), w, match,
+                                    mismatch, step, nbins, res.ctypes.data,
+                                    nthreads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle_plot_digest rejected its arguments")
+    return int(res[0]), res[1:].astype(np.int64)
+
+
+def _blow(match: int, mismatch: int) -> tuple[int, int]:
+    if (match, mismatch) == (1, 0) or (match >= 2 and 1 <= mismatch < match):
+        return match, mismatch
+    raise ValueError("the bit-parallel reference takes LCS or {nu, mu, 0} with 0 < mu < nu")
+
+
+def blcs_plot(x, y, w: int, match: int = 1, mismatch: int = 0, step: int = 1,
+              nthreads: int | None = None) -> np.ndarray:
+    """The plot by bit-parallel LCS of the (blown-up) window pairs."""
+    x, y = _u8(x), _u8(y)
+    nu, mu = _blow(match, mismatch)
+    rows, cols = step_shape(len(x), len(y), w, step)
+    out = np.zeros((rows, cols), dtype=np.int32)
+    if rows and cols:
+        rc = _load().oracle_blcs_plot(x.ctypes.data, len(x), y.ctypes.data, len(y), w, nu, mu,
+                                      step, out.ctypes.data, cols, nthreads or default_threads())
+        if rc != 0:
+            raise ValueError("oracle_blcs_plot rejected its arguments")
+    return out
+
+
+def blcs_digest(x, y, w: int, match: int = 1, mismatch: int = 0, step: int = 1,
+                nbins: int | None = None, nthreads: int | None = None):
+    """(checksum, histogram) of the whole plot by bit-parallel LCS."""
+    x, y = _u8(x), _u8(y)
+    nu, mu = _blow(match, mismatch)
+    nbins = match * w + 1 if nbins is None else nbins
+    res = np.zeros(1 + nbins, dtype=np.uint64)
+    rc = _load().oracle_blcs_digest(x.ctypes.data, len(x), y.ctypes.data, len(y), w, nu, mu,
+                                    step, nbins, res.ctypes.data, nthreads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle_blcs_digest rejected its arguments")
+    return int(res[0]), res[1:].astype(np.int64)
 
 
 # ---------------------------------------------------------------------------

@@ -161,3 +161,73 @@ int oracle_samples(const uint8_t *x, int64_t m, const uint8_t *y, int64_t n,
     b.ii = ii; b.jj = jj;
     return run_split(sample_worker, b, count, nthreads);
 }
+
+/* ---------------------------------------------------------------------------
+ * Digest of a whole plot without storing it (for plots too large to hold):
+ *     result[0]     = sum over cells of P[r][j] * (r*2654435761 + j*40503 + 1)
+ *                     mod 2^64
+ *     result[1 + v] = number of cells with value v, for v < nbins
+ * over plot rows r = 0, 1, ... where row r is the x-window starting at
+ * r * step (step 1: the full plot).  Each value is the recurrence above.
+ * ------------------------------------------------------------------------- */
+
+typedef struct {
+    const uint8_t *x, *y;
+    int64_t w, step, cols;
+    int32_t match, mismatch;
+    int32_t nbins;
+    uint64_t *acc;
+    int64_t r0, r1;
+} digest_job_t;
+
+static void *digest_worker(void *arg)
+{
+    digest_job_t *jb = (digest_job_t *)arg;
+    int32_t *row = (int32_t *)malloc(sizeof(int32_t) * (size_t)(jb->w + 1));
+    for (int64_t r = jb->r0; r < jb->r1; ++r) {
+        const uint64_t wr = (uint64_t)r * 2654435761ull + 1ull;
+        for (int64_t j = 0; j < jb->cols; ++j) {
+            const int64_t v = oracle_pair_score(jb->x + r * jb->step, jb->w, jb->y + j, jb->w,
+                                                jb->match, jb->mismatch, row);
+            jb->acc[0] += (uint64_t)v * (wr + (uint64_t)j * 40503ull);
+            if (v >= 0 && v < jb->nbins) jb->acc[1 + v] += 1;
+        }
+    }
+    free(row);
+    return NULL;
+}
+
+int oracle_plot_digest(const uint8_t *x, int64_t m, const uint8_t *y, int64_t n, int64_t w,
+                       int32_t match, int32_t mismatch, int64_t step, int32_t nbins,
+                       uint64_t *result, int nthreads)
+{
+    if (w < 1 || m < 0 || n < 0 || step < 1 || nbins < 0) return -1;
+    for (int32_t k = 0; k <= nbins; ++k) result[k] = 0;
+    const int64_t rows = m > w ? (m - w + step - 1) / step : 0;
+    const int64_t cols = n > w ? n - w : 0;
+    if (rows == 0 || cols == 0) return 0;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if (nthreads > rows) nthreads = (int)rows;
+    uint64_t *acc = (uint64_t *)calloc((size_t)nthreads * (size_t)(1 + nbins), sizeof(uint64_t));
+    pthread_t th[256];
+    digest_job_t jobs[256];
+    for (int t = 0; t < nthreads; ++t) {
+        digest_job_t *jb = &jobs[t];
+        jb->x = x; jb->y = y; jb->w = w; jb->step = step; jb->cols = cols;
+        jb->match = match; jb->mismatch = mismatch; jb->nbins = nbins;
+        jb->acc = acc + (size_t)t * (size_t)(1 + nbins);
+        jb->r0 = rows * t / nthreads;
+        jb->r1 = rows * (t + 1) / nthreads;
+        if (pthread_create(&th[t], NULL, digest_worker, jb) != 0) {
+            digest_worker(jb);
+            th[t] = 0;
+        }
+    }
+    for (int t = 0; t < nthreads; ++t)
+        if (th[t]) pthread_join(th[t], NULL);
+    for (int t = 0; t < nthreads; ++t)
+        for (int32_t k = 0; k <= nbins; ++k) result[k] += acc[(size_t)t * (size_t)(1 + nbins) + k];
+    free(acc);
+    return 0;
+}

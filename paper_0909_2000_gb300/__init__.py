@@ -19,7 +19,7 @@ import threading
 
 __all__ = [
     "load", "ApError", "LCS", "SCORE", "plot_shape", "plot_plan", "alignment_plot",
-    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "alignment_plot_step", "alignment_plot_host", "set_chunk", "set_lanes_per_strip", "Batch", "Server", "DOT_DTYPE_FIELDS",
+    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "alignment_plot_step", "alignment_plot_host", "set_chunk", "set_band_rows", "set_lanes_per_strip", "Batch", "Server", "DOT_DTYPE_FIELDS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -97,6 +97,7 @@ def _declare(lib):
     sigs = {
         "ap_set_chunk": [i64],
         "ap_set_lanes_per_strip": [i32],
+        "ap_set_band_rows": [i64],
         "ap_plot_shape": [i64, i64, i32, i64p, i64p],
         "ap_plot_plan": [i64, i64, i32, sc, ctypes.POINTER(ap_plan)],
         "ap_alignment_plot": [p, i64, p, i64, i32, sc, p, i32, i64, p],
@@ -186,6 +187,12 @@ def _dev_u8(t, name):
 def set_chunk(chunk: int) -> None:
     """Force plot columns per tile (0 = automatic); results do not change."""
     _check(load().ap_set_chunk(int(chunk)))
+
+
+def set_band_rows(rows: int) -> None:
+    """Force the band height (plot rows) of the banded calls -- dots, plots
+    into host memory, server jobs (0 = automatic); results do not change."""
+    _check(load().ap_set_band_rows(int(rows)))
 
 
 def set_lanes_per_strip(groups: int) -> None:
@@ -410,9 +417,19 @@ def plot_dots_noalloc(plot, threshold: int, dots, cap: int | None = None, stream
     ``dots`` is the caller's output buffer (CUDA int32 tensor of shape
     (capacity, 3)).  Returns (dots, count); raises ApError(AP_E_OVERFLOW) if
     the buffer is too small (the count is still reported on the error)."""
+    import torch
+    if plot.dim() != 2 or not plot.is_cuda or plot.element_size() not in (1, 2):
+        raise ValueError("plot must be a 2-D CUDA tensor of 8- or 16-bit elements")
     rows, cols = plot.shape
+    if cols > 1 and plot.stride(1) != 1:
+        raise ValueError("plot rows must be contiguous (stride(1) == 1)")
+    if (not isinstance(dots, torch.Tensor) or dots.dtype != torch.int32 or dots.dim() != 2
+            or dots.shape[1] != 3 or not dots.is_contiguous() or dots.device != plot.device):
+        raise ValueError("dots must be a contiguous (N, 3) int32 CUDA tensor on the plot's device")
+    capacity = dots.shape[0] if cap is None else int(cap)
+    if not 0 <= capacity <= dots.shape[0]:
+        raise ValueError("cap = %d outside 0..%d (the dot buffer's rows)" % (capacity, dots.shape[0]))
     cnt = ctypes.c_int64()
-    capacity = dots.shape[0] if cap is None else cap
     status = load().ap_plot_dots_noalloc(ctypes.c_void_p(plot.data_ptr()), plot.element_size(), rows,
                                          cols, plot.stride(0) if rows > 1 else cols, int(threshold),
                                          ctypes.c_void_p(dots.data_ptr()), capacity,

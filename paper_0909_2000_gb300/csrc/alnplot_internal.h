@@ -30,6 +30,11 @@ ap_status check_output(const Plan &pl, const void *x, const void *y, const void 
 
 int current_device();
 
+// Band height (plot rows) of the banded calls: `automatic` unless
+// ap_set_band_rows has forced one; whole strip groups of `spw` strips, at
+// most the plot's rows rounded up to a strip group.
+int64_t band_rows_for(int64_t automatic, int64_t spw, int64_t rows);
+
 // Dots of a plot region [rows x cols] (ld elements per row) in row-major order,
 // appended after *running dots; *running (device) grows by the region's count.
 // counts: device, rows int32; offsets: device, rows int64.

@@ -14,6 +14,18 @@ namespace ap {
 static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_chunk_override{0};
 static std::atomic<int32_t> g_groups_override{0};
+static std::atomic<int64_t> g_band_override{0};
+
+int64_t band_rows_override() { return g_band_override.load(); }
+
+int64_t band_rows_for(int64_t automatic, int64_t spw, int64_t rows)
+{
+    int64_t br = automatic;
+    const int64_t o = band_rows_override();
+    if (o > 0) br = (o + spw - 1) / spw * spw;
+    br = std::max<int64_t>(spw, br / spw * spw);
+    return std::min(br, std::max<int64_t>(spw, (rows + spw - 1) / spw * spw));
+}
 
 ap_status fail(ap_status s, const char *fmt, ...)
 {
@@ -116,11 +128,8 @@ DotsLayout dots_layout(const Plan &pl)
     DotsLayout L;
     L.elem = pl.max_value > 255 ? 2 : 1;
     L.band_ld = (pl.cols + 31) / 32 * 32;   // whole 32-byte sectors per row block
-    const int64_t spw = pl.strips_per_warp;
-    const int64_t all_rows = (pl.rows + spw - 1) / spw * spw;
-    int64_t br = kBandBudget / std::max<int64_t>(1, L.band_ld * L.elem);
-    br = std::max<int64_t>(spw, br / spw * spw);
-    L.band_rows = std::min(br, std::max<int64_t>(spw, all_rows));
+    L.band_rows = band_rows_for(kBandBudget / std::max<int64_t>(1, L.band_ld * L.elem),
+                                pl.strips_per_warp, pl.rows);
     L.plot_off = 0;
     L.counts_off = align256(L.band_rows * L.band_ld * L.elem);
     L.offsets_off = L.counts_off + align256(L.band_rows * 4);
@@ -160,6 +169,13 @@ ap_status ap_set_chunk(int64_t chunk)
 {
     if (chunk < 0) return fail(AP_E_INVAL, "chunk = %lld: must be >= 0", (long long)chunk);
     g_chunk_override.store(chunk);
+    return AP_OK;
+}
+
+ap_status ap_set_band_rows(int64_t rows)
+{
+    if (rows < 0) return fail(AP_E_INVAL, "band rows = %lld: must be >= 0", (long long)rows);
+    g_band_override.store(rows);
     return AP_OK;
 }
 

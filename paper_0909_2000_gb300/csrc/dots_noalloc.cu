@@ -9,7 +9,6 @@
 // array inside the library.  Every GPU that loads the library holds the
 // array until the process exits.
 #include <cstdio>
-#include <mutex>
 
 #include "alnplot_internal.h"
 
@@ -25,33 +24,23 @@ constexpr int64_t kScratchBytes = kRunningOff + 256;           // running total
 
 // The scratch.  In host code this name is only a host-side stand-in for the
 // device array, never a device address: the address comes from
-// cudaGetSymbolAddress below, once per device.
+// cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_dots_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_dev[kMaxDevices];   // device address of g_dots_scratch, per device
-
-// Device address of the scratch on the current device.  The first call on a
-// device looks it up (with that device current) and remembers it.
+// Device address of the scratch in the current context.  It is looked up
+// on every call, with the calling thread's device current: the first lookup
+// in a context loads this file's module (and with it the array), and a
+// lookup per call never hands out an address from a context that
+// cudaDeviceReset has since destroyed.  Next to the stream synchronisation
+// every call makes, the lookup costs nothing.
 ap_status scratch_address(void **out)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices)
-        return fail(AP_E_UNSUPPORTED, "device %d: the static dots scratch covers devices 0..%d",
-                    dev, kMaxDevices - 1);
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_dev[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_dots_scratch);
-        if (e != cudaSuccess || !p)
-            return fail_cuda(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
-                             "cudaGetSymbolAddress of the static dots scratch");
-        g_scratch_dev[dev] = p;
-    }
-    *out = g_scratch_dev[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_dots_scratch);
+    if (e != cudaSuccess || !p)
+        return fail_cuda(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                         "cudaGetSymbolAddress of the static dots scratch");
+    *out = p;
     return AP_OK;
 }
 
@@ -72,12 +61,15 @@ extern "C" ap_status ap_plot_dots_noalloc(const void *plot, int32_t elem_bytes, 
         return fail(AP_E_NOMEM, "ap_plot_dots_noalloc: %lld plot rows exceed the static scratch "
                     "(at most %lld rows); use ap_plot_dots with a workspace",
                     (long long)rows, (long long)kMaxRows);
-    *count = 0;
-    if (rows == 0 || cols == 0) return AP_OK;
-    if (!plot) return fail(AP_E_INVAL, "ap_plot_dots_noalloc: null plot");
+    // The address lookup comes before the empty-plot return, so that a call
+    // with rows = 0 loads the array on this device without touching a plot:
+    // callers warm a device up that way at start-up, before any capture.
     void *base = nullptr;
     ap_status s = scratch_address(&base);
     if (s != AP_OK) return s;
+    *count = 0;
+    if (rows == 0 || cols == 0) return AP_OK;
+    if (!plot) return fail(AP_E_INVAL, "ap_plot_dots_noalloc: null plot");
     char *ws = (char *)base;
     int32_t *counts = (int32_t *)ws;
     int64_t *offsets = (int64_t *)(ws + kOffsetsOff);

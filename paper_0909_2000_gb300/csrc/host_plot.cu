@@ -35,10 +35,8 @@ HostLayout host_layout(const Plan &pl, int64_t m, int64_t n, int elem, int64_t d
 {
     HostLayout L;
     L.band_ld = (pl.cols + 31) / 32 * 32;
-    const int64_t spw = pl.strips_per_warp;
-    int64_t br = kHostBand / std::max<int64_t>(1, L.band_ld * elem);
-    br = std::max<int64_t>(spw, br / spw * spw);
-    L.band_rows = std::min(br, (pl.rows + spw - 1) / spw * spw);
+    L.band_rows = band_rows_for(kHostBand / std::max<int64_t>(1, L.band_ld * elem),
+                                pl.strips_per_warp, pl.rows);
     int64_t o = 0;
     L.x_off = o;
     o += align256(m);

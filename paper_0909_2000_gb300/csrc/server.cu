@@ -89,10 +89,8 @@ void layout(Job &j, int64_t band)
     const Plan &pl = j.plan;
     j.elem = pl.max_value > 255 ? 2 : 1;
     j.band_ld = (pl.cols + 31) / 32 * 32;
-    const int64_t spw = pl.strips_per_warp;
-    int64_t br = band / std::max<int64_t>(1, j.band_ld * j.elem);
-    br = std::max<int64_t>(spw, br / spw * spw);
-    j.band_rows = std::min(br, (pl.rows + spw - 1) / spw * spw);
+    j.band_rows = band_rows_for(band / std::max<int64_t>(1, j.band_ld * j.elem),
+                                pl.strips_per_warp, pl.rows);
     int64_t o = align256((int64_t)j.x.size());
     j.off_y = o;
     o += align256((int64_t)j.y.size());

@@ -158,6 +158,7 @@ class Pair:
     threshold: int | None = None
     name: str = ""
     planted: list = field(default_factory=list)
+    step: int = 1                   # vertical step: plot row r is x-window r * step
 
 
 def dna_plot_512(seed: int = 0) -> Pair:
@@ -190,6 +191,18 @@ def dna_plot_20k_w256(seed: int = 0) -> Pair:
     c = dna_plot_100k(seed, 20_000, 20_000, 256, 4, 2000)
     c.threshold = threshold_08(256)
     c.name = "lcs_dna_20k_w256"
+    return c
+
+
+def dna_score_80k_step5(seed: int = 0) -> Pair:
+    """The shape of the paper's largest Table 1 runs: m = n = 80,000, w = 100,
+    scores (1, 0, -1/2) as {2,1,0}, vertical step 5 (DNA with 16 planted
+    homologous segments of length 2000 stands in for the absent sequences)."""
+    c = dna_plot_100k(seed, 80_000, 80_000, 100, 16, 2000)
+    c.scores = (2, 1)
+    c.threshold = None
+    c.step = 5
+    c.name = "score_dna_80k_w100_step5"
     return c
 
 

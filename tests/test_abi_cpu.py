@@ -125,3 +125,28 @@ def test_chunk_count_minimises_rounds_times_tile_length():
         best = min(cost(ch) for ch in chunks)
         assert pl["chunk"] % 32 == 0
         assert cost(pl["chunk"]) <= best * (1 + 1e-9), (m, n, w, pl["chunk"])
+
+
+def test_band_rows_override_sets_the_banded_workspaces():
+    """ap_set_band_rows (host only): the dots workspace holds one band, so its
+    size follows the forced band height, rounded up to whole strip groups."""
+    base = ap._scores(ap.LCS)
+    import ctypes
+    lib = ap.load()
+
+    def ws(m, n, w):
+        b = ctypes.c_int64()
+        ap._check(lib.ap_dots_workspace_size(m, n, w, ctypes.byref(base), ctypes.byref(b)))
+        return b.value
+    auto = ws(5000, 5000, 40)
+    try:
+        ap.set_band_rows(100)           # 128-strip groups: one group per band
+        small = ws(5000, 5000, 40)
+        ap.set_band_rows(129)           # two groups
+        two = ws(5000, 5000, 40)
+    finally:
+        ap.set_band_rows(0)
+    assert small < two < auto == ws(5000, 5000, 40)
+    with pytest.raises(ap.ApError) as e:
+        ap.set_band_rows(-1)
+    assert e.value.status == ap.AP_E_INVAL

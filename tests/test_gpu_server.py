@@ -97,7 +97,8 @@ def test_admission_by_memory_budget(cuda_lib):
 def test_wait_timeout_cancel_and_overflow(cuda_lib):
     ap = cuda_lib
     srv = ap.Server(mem_budget=4 << 30, max_slots=1)
-    big_x, big_y = synth.dna(3, 1, 60000), synth.dna(3, 2, 60000)
+    big_x = synth.dna(3, 1, 60000)
+    big_y, _ = synth.plant(big_x, synth.dna(3, 2, 60000), 6, 2000, 3, 11, synth.DNA, 0.1, 0.05)
     t_big = srv.submit(big_x, big_y, 100, 80)
     t_queued = srv.submit(big_x[:5000], big_y[:5000], 100, 80)
     assert srv.wait(t_big, 0) == ap.AP_E_TIMEOUT          # a bounded wait returns
@@ -105,7 +106,19 @@ def test_wait_timeout_cancel_and_overflow(cuda_lib):
     srv.cancel(t_queued)
     assert srv.wait(t_queued, 10000) == ap.AP_E_CANCELLED
     assert srv.wait(t_big, 120000) == ap.AP_OK
-    srv.fetch(t_big)
+    # the big job runs several plot bands (its band is a share of the
+    # budget): its dots equal the plain call's, and seeded oracle samples
+    # confirm dot values and non-dots below the threshold
+    _, cnt, dots = srv.fetch(t_big)
+    plain = reference(ap, big_x, big_y, 100, 80, (1, 0, 0))
+    assert cnt == len(plain) > 1000 and np.array_equal(dots, plain)
+    pick = dots[synth.below(3, 40, 300, len(dots))]
+    assert np.array_equal(oracle.samples(big_x, big_y, 100, pick[:, 0], pick[:, 1]), pick[:, 2])
+    ii, jj = synth.below(3, 41, 300, 59900), synth.below(3, 42, 300, 59900)
+    dotset = set(map(tuple, dots[:, :2].tolist()))
+    off = [(i, j) for i, j in zip(ii.tolist(), jj.tolist()) if (i, j) not in dotset]
+    vals = oracle.samples(big_x, big_y, 100, [i for i, _ in off], [j for _, j in off])
+    assert bool((vals < 80).all())
     # overflow: the full count and the first max_dots dots
     x = synth.dna(4, 1, 800)
     y, _ = synth.plant(x, synth.dna(4, 2, 900), 1, 400, 4, 5, synth.DNA, 0.05, 0.0)

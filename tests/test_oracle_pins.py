@@ -116,3 +116,37 @@ def test_blow_up_reduction_small_rational_scores(nu, mu):
             assert pins.lcs_bruteforce(blow(a), blow(b)) == brute_align
         assert oracle.pair_score(a, b, nu, mu) == brute_align
         assert oracle.pair_score(blow(a), blow(b), 1, 0) == brute_align
+
+
+# ---- the bit-parallel second reference (large-plot digests) ----
+
+def blcs_plot(x, y, w, match, mismatch):
+    return oracle.blcs_plot(x, y, w, match, mismatch, nthreads=3)
+
+
+def test_battery_bit_parallel_reference():
+    assert pins.pin_battery(blcs_plot) == []
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bit_parallel_reference_equals_the_dynamic_programme(seed):
+    """Random shapes across the word boundaries of the bit-parallel method
+    (blown-up windows of 63, 64, 65, 128, 129 ... characters), all byte
+    values, LCS and {nu, mu, 0}, with and without a vertical step."""
+    rng = synth.below(seed, 1, 8, 1 << 30)
+    alph = [b"AC", b"ACGT", bytes(range(256)), b"ACDEFGHIKLMNPQRSTVWY"][seed % 4]
+    cases = [(1, 0, 63), (1, 0, 64), (1, 0, 65), (1, 0, 128), (1, 0, 129), (2, 1, 32), (2, 1, 33),
+             (2, 1, 64), (3, 2, 43), (4, 1, 16), (4, 3, 33), (1, 0, 300)]
+    for k, (nu, mu, w) in enumerate(cases):
+        m = w + 1 + int(rng[k % 8]) % 60
+        n = w + 1 + int(rng[(k + 3) % 8]) % 70
+        x = _rand_alpha(seed * 100 + k, 1, m, alph)
+        y = _rand_alpha(seed * 100 + k, 2, n, alph)
+        step = 1 + k % 3
+        want = oracle.plot(x, y, w, nu, mu)[::step]
+        got = oracle.blcs_plot(x, y, w, nu, mu, step)
+        assert got.shape == want.shape and np.array_equal(got, want), (nu, mu, w, step)
+
+
+def _rand_alpha(seed, stream, n, alph):
+    return synth.alphabet_string(seed, stream, n, np.frombuffer(alph, dtype=np.uint8))
