@@ -56,16 +56,21 @@ typedef enum ap_status {
  *              where S is the (1, 0, -1/2) score.  Computed as the LCS of the
  *              '$'-interleaved windows (Section 2), with Definition 3.2's
  *              (w, 2) restriction.
- *   {m, x, 0}  2 <= m <= 4, 1 <= x < m: the same construction for other small
- *              rational scores (Section 2 reduces them to LCS by enlarging
- *              the input strings by a constant factor): every character
- *              becomes x copies of '$' followed by m - x copies of itself,
- *              and P = the LCS of the blown-up windows = the best alignment
- *              score, x w <= P <= m w.
- *              Windows up to 32 (8-bit lanes) or 128 (16-bit lanes).
- * A scheme (a, b, g) with g < 0 maps to {a - 2g, b - 2g, 0} after scaling to
- * integers (and the plot value to S - 2wg).  Other normalised pairs, and
- * {m, 0, 0} with m > 1 (m times the LCS), return AP_E_UNSUPPORTED.
+ *   {m, x, 0}  other small rational scores (Section 2 reduces them to LCS by
+ *              enlarging the input strings by a constant factor).  With
+ *              g = gcd(m, x), every score under {m, x, 0} is g times its score
+ *              under {m/g, x/g, 0}, so the plot is g times the reduced
+ *              scheme's plot; the reduced scheme with m/g >= 2 is combed as
+ *              the LCS of blown-up windows, every character becoming x/g
+ *              copies of '$' followed by m/g - x/g copies of itself.  Built:
+ *              m/g <= 4 -- so {m, 0, 0} (m times the LCS, g = m) for any m,
+ *              {2k, k, 0}, {3k, k, 0}, {3k, 2k, 0}, {4k, k, 0}, {4k, 3k, 0}.
+ *              x w <= P <= m w.  Windows: as LCS for m/g = 1, as {2,1,0} for
+ *              m/g = 2, up to 256 for m/g = 3, 4.
+ * A scheme (a, b, c) with c < 0 maps to {a - 2c, b - 2c, 0} after scaling to
+ * integers (and the plot value to S - 2wc).  Other normalised pairs
+ * (m/g >= 5) return AP_E_UNSUPPORTED; so do plots whose largest value m w
+ * exceeds 65535.
  */
 typedef struct ap_scores {
     int32_t match;

@@ -60,12 +60,13 @@ def _variants():
     # {2,1,0}, 15-bit pair keys, 8 threads: w <= 256
     for rp in range(16, 33, 4):
         v.append(("U16Lanes", 15, 16, 2 * rp, 8, 2, 1, 4))
-    # other blow-ups {nu, mu, 0}, nu = 3, 4: w <= 32 on one thread (8-bit
-    # lanes), w <= 128 on 8 threads (16-bit lanes)
-    for nu, mu in ((3, 1), (3, 2), (4, 1), (4, 2), (4, 3)):
+    # other blow-ups {nu, mu, 0} in lowest terms (schemes with a common factor
+    # g comb their reduced form and scale the plot by g), nu = 3, 4: w <= 32 on
+    # one thread (8-bit lanes), w <= 256 on 8 threads (16-bit lanes)
+    for nu, mu in ((3, 1), (3, 2), (4, 1), (4, 3)):
         for rp in (8, 16, 24, 32):
             v.append(("U8Lanes", 7, 8, nu * rp, 1, nu, mu, 8))
-        for rp in (4, 8, 12, 16):
+        for rp in range(4, 33, 4):
             v.append(("U16Lanes", 15, 16, nu * rp, 8, nu, mu, 4))
     v = [t + (False,) for t in v]
     # vertical step h > 1 (one x word per unit): LCS w <= 120 and {2,1,0} w <= 120
@@ -96,7 +97,7 @@ def _generate() -> list[str]:
             lines.append("    AP_VARIANT(%s, %d, %d, %d, %d, %d, %d, %d, %s)," % (
                 lanes, kbits, bits, r, g, nu, mu, padu, "true" if xr else "false"))
         if not part:
-            lines.append("    {0, 0, 0, 0, 0, 0, 0, nullptr, nullptr},")
+            lines.append("    {0, 0, 0, 0, 0, 0, 0, 0, nullptr, nullptr},")
         lines += ["};", "const int kNumVariants%d = %d;" % (k, len(part)), "}  // namespace ap", ""]
         paths.append(_write_if_changed(os.path.join(gen, "variants_%02d.cu" % k), "\n".join(lines)))
     table = ['#include <vector>', '#include <mutex>', '#include "variants.h"', "namespace ap {"]
@@ -122,8 +123,11 @@ def _write_if_changed(path: str, text: str) -> str:
 
 
 def _flags():
+    # AP_KERNEL_DIGEST keys the batch autotuner's persistent cache to these
+    # comb kernels
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
+                   "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE,
+                   "-DAP_KERNEL_DIGEST=\"comb-%s\"" % kernel_digest()]
 
 
 def _deps_digest() -> str:

@@ -15,14 +15,15 @@ ap_status fail_cuda(cudaError_t e, const char *what);
 
 struct Plan;
 
-// Scores -> blow-up {nu, mu, 0} (nu = 1: LCS); errors for other schemes.
-ap_status score_mode(const ap_scores *sc, int *nu, int *mu);
+// Scores -> blow-up {nu, mu, 0} of the gcd-reduced scheme (nu = 1: LCS) and
+// the scale g = gcd(match, mismatch) of the plot; errors for other schemes.
+ap_status score_mode(const ap_scores *sc, int *nu, int *mu, int *scale);
 
 // Validated plan of one plot: variant (groups > 0 requests threads per strip
-// group), tiling (chunk > 0 forces the chunk), vertical step (plot row r is the
-// x-window at r * step).
+// group, lane_bits > 0 a lane format), tiling (chunk > 0 forces the chunk),
+// vertical step (plot row r is the x-window at r * step).
 ap_status plan_plot(int64_t m, int64_t n, int32_t w, const ap_scores *scores, int groups,
-                    int64_t chunk, Plan *pl, int64_t step = 1);
+                    int64_t chunk, Plan *pl, int64_t step = 1, int lane_bits = 0);
 
 // Output-argument checks shared by the plain and batched calls.
 ap_status check_output(const Plan &pl, const void *x, const void *y, const void *out,

@@ -43,23 +43,35 @@ ap_status fail_cuda(cudaError_t e, const char *what)
     return fail(AP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// Scores -> blow-up {nu, mu, 0}.  Normalised form: gap 0, 0 <= mismatch < match.
-ap_status score_mode(const ap_scores *sc, int *nu, int *mu)
+// Scores -> blow-up {nu, mu, 0} and scale.  Normalised form: gap 0,
+// 0 <= mismatch < match.  Every alignment score of {a, b, 0} is g times its
+// score under {a/g, b/g, 0} with g = gcd(a, b), so the plot is g times the
+// reduced scheme's plot: {m, 0, 0} is m x LCS, {4, 2, 0} is 2 x {2, 1, 0}.
+// The reduced scheme is combed through the Section 2 blow-up (nu = 1: LCS).
+ap_status score_mode(const ap_scores *sc, int *nu, int *mu, int *scale)
 {
     *nu = 1;
     *mu = 0;
+    *scale = 1;
     if (!sc) return AP_OK;
     if (sc->gap != 0 || sc->mismatch < 0 || sc->mismatch >= sc->match)
         return fail(AP_E_INVAL, "scores {%d,%d,%d} are not normalised (need gap 0, "
                     "0 <= mismatch < match)", sc->match, sc->mismatch, sc->gap);
-    if (sc->match == 1) return AP_OK;   // {1,0,0}: LCS
-    if (sc->match <= 4 && sc->mismatch >= 1) {
-        *nu = sc->match;
-        *mu = sc->mismatch;
-        return AP_OK;
+    int a = sc->match, b = sc->mismatch;
+    while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
     }
-    return fail(AP_E_UNSUPPORTED, "scores {%d,%d,0}: built are {1,0,0} and {m,x,0} with "
-                "2 <= m <= 4, 1 <= x < m", sc->match, sc->mismatch);
+    const int g = a;                                     // gcd(match, mismatch)
+    const int rn = sc->match / g, rm = sc->mismatch / g;
+    if (rn > 4 || (int64_t)sc->match > 65535)
+        return fail(AP_E_UNSUPPORTED, "scores {%d,%d,0}: built are schemes whose reduced form "
+                    "{m/g, x/g, 0} (g = gcd(m, x)) has m/g <= 4", sc->match, sc->mismatch);
+    *nu = rn;
+    *mu = rm;
+    *scale = g;
+    return AP_OK;
 }
 
 int current_device()
@@ -73,17 +85,19 @@ int current_device()
 }
 
 ap_status plan_plot(int64_t m, int64_t n, int32_t w, const ap_scores *scores, int groups,
-                    int64_t chunk, Plan *pl, int64_t step)
+                    int64_t chunk, Plan *pl, int64_t step, int lane_bits)
 {
     if (step < 1) return fail(AP_E_INVAL, "step = %lld: must be >= 1", (long long)step);
     if (w < 1) return fail(AP_E_INVAL, "w = %d: the window length must be >= 1", w);
     if (m < 0 || n < 0) return fail(AP_E_INVAL, "negative sequence length");
-    int nu = 1, mu = 0;
-    ap_status s = score_mode(scores, &nu, &mu);
+    int nu = 1, mu = 0, scale = 1;
+    ap_status s = score_mode(scores, &nu, &mu, &scale);
     if (s != AP_OK) return s;
     std::string why;
-    if (!choose_variant(w, nu, mu, groups, step, pl, &why))
+    if (!choose_variant(w, nu, mu, groups, step, pl, &why, lane_bits))
         return fail(AP_E_UNSUPPORTED, "%s", why.c_str());
+    pl->scale = scale;
+    pl->max_value = nu * scale * w;                      // = match * w
     // plot rows: x-windows 0, step, 2 step, ... below m - w
     const int64_t rows = m > w ? (m - w + step - 1) / step : 0;
     const int64_t cols = std::max<int64_t>(0, n - w);
@@ -98,6 +112,8 @@ ap_status check_output(const Plan &pl, const void *x, const void *y, const void 
         return fail(AP_E_INVAL, "out_elem_bytes = %d: must be 1 or 2", out_elem_bytes);
     if (out_elem_bytes == 1 && pl.max_value > 255)
         return fail(AP_E_INVAL, "uint8 output cannot hold values up to %d", pl.max_value);
+    if (pl.max_value > 65535)
+        return fail(AP_E_INVAL, "uint16 output cannot hold values up to %d", pl.max_value);
     if (pl.rows == 0 || pl.cols == 0) return AP_OK;   // empty plot
     if (!x || !y || !out) return fail(AP_E_INVAL, "null pointer");
     if (ld < pl.cols)

@@ -13,10 +13,16 @@
 //     per strip) for every window class when the batch is created.
 // Each tile is combed exactly as a plain launch combs it, so every job's plot
 // is bit-identical to ap_alignment_plot's.
+#include <sys/stat.h>
+
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -38,9 +44,92 @@ struct Group {
     cudaEvent_t done = nullptr;
 };
 
-// Process-wide cache of tuned schedules: (nu, mu, w, SMs) -> (groups, chunk).
+// A tuned schedule of one window class: lane format (strips per register),
+// threads per strip group and column chunk.
+struct Schedule {
+    int lane_bits = 0;
+    int groups = 0;
+    int64_t chunk = 0;
+};
+
+// Tuned schedules, keyed by the comb kernels' build digest, the device (name
+// and SM count) and the window class (nu, mu, w).  Kept for the process and,
+// unless AP_TUNE_CACHE=off, in a text file (AP_TUNE_CACHE, else
+// $XDG_CACHE_HOME/alnplot/tune.txt or ~/.cache/alnplot/tune.txt), one line
+// per class, so that later processes on the same kind of GPU skip the tuning.
+#ifndef AP_KERNEL_DIGEST
+#define AP_KERNEL_DIGEST "unversioned"
+#endif
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, std::pair<int, int64_t>> g_tuned;
+std::map<std::string, Schedule> g_tuned;
+bool g_cache_loaded = false;
+
+std::string tune_cache_path()
+{
+    const char *e = getenv("AP_TUNE_CACHE");
+    if (e && *e) return strcmp(e, "off") == 0 ? std::string() : std::string(e);
+    std::string dir;
+    if (const char *x = getenv("XDG_CACHE_HOME")) dir = x;
+    else if (const char *h = getenv("HOME")) dir = std::string(h) + "/.cache";
+    else return std::string();
+    mkdir(dir.c_str(), 0755);
+    dir += "/alnplot";
+    mkdir(dir.c_str(), 0755);
+    return dir + "/tune.txt";
+}
+
+// Called with g_tune_mu held.
+void load_tune_cache()
+{
+    if (g_cache_loaded) return;
+    g_cache_loaded = true;
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        char key[400];
+        Schedule sc;
+        long long chunk = 0;
+        if (sscanf(line, "%399[^|]| %d %d %lld", key, &sc.lane_bits, &sc.groups, &chunk) == 4 && chunk > 0) {
+            sc.chunk = chunk;
+            g_tuned[key] = sc;
+        }
+    }
+    fclose(f);
+}
+
+// Called with g_tune_mu held.
+void store_tune_cache(const std::string &key, const Schedule &sc)
+{
+    g_tuned[key] = sc;
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "%s| %d %d %lld\n", key.c_str(), sc.lane_bits, sc.groups, (long long)sc.chunk);
+    fclose(f);
+}
+
+std::string tune_key(int device, int nu, int mu, int w)
+{
+    cudaDeviceProp prop;
+    std::string name = "unknown";
+    int sms = 0;
+    if (cudaGetDeviceProperties(&prop, std::max(0, device)) == cudaSuccess) {
+        name = prop.name;
+        sms = prop.multiProcessorCount;
+    } else {
+        cudaGetLastError();
+    }
+    for (char &c : name)
+        if (c == ' ' || c == '|') c = '_';
+    char buf[400];
+    snprintf(buf, sizeof buf, "%s %s sms=%d nu=%d mu=%d w=%d ", AP_KERNEL_DIGEST, name.c_str(), sms,
+             nu, mu, w);
+    return buf;
+}
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -175,37 +264,67 @@ cudaError_t upload_params(ap_batch *b)
     return cudaMemcpy(b->d_params, hp.data(), sizeof(CombParams) * hp.size(), cudaMemcpyHostToDevice);
 }
 
-// Autotune one window class: try (threads per strip, chunk) candidates on the
-// class's jobs, timing one persistent launch each; returns the fastest.
-ap_status tune_class(ap_batch *b, const std::vector<int> &idx, int nu, int w,
-                     std::pair<int, int64_t> *best, double *tune_ms)
+// Autotune one window class: try lane formats x threads per strip group x
+// column chunks on a sample of the class's jobs (every fourth job of the
+// class, in job order, when it has eight or more), timing one persistent
+// launch each after one untimed launch; returns the fastest schedule.
+ap_status tune_class(ap_batch *b, const std::vector<int> &idx, int nu, int w, Schedule *best,
+                     double *tune_ms)
 {
-    std::vector<int> groups_c = {0};
-    if (nu == 1 && w <= 120) groups_c = {1, 2};
+    // Candidate (lane bits, threads per strip group); 0 lane bits = the
+    // default format for the window.  8-bit lanes always win over 16-bit
+    // lanes up to w = 120 (twice the strips per instruction), so those are
+    // not timed there.
+    std::vector<std::pair<int, int>> cands;
+    if (nu == 1) {
+        std::vector<int> lbs;
+        if (w <= 120) lbs = {8};
+        else if (w <= 254) lbs = {8, 16};
+        else if (w > 256 && w <= 480) lbs = {10, 16};
+        else lbs = {16};
+        for (int lb : lbs)
+            for (int g : {1, 2, 4, 8}) cands.push_back({lb, g});
+    } else {
+        for (int g : {1, 2, 4, 8}) cands.push_back({0, g});
+    }
     std::vector<int64_t> chunks_c = {1024, 4096, 16384};
+    std::vector<int> sample;
+    for (size_t k = 0; k < idx.size(); ++k)
+        if (idx.size() < 8 || k % 4 == 0) sample.push_back(idx[k]);
     float best_ms = 1e30f;
-    *best = {0, default_chunk(w)};
+    best->lane_bits = 0;
+    best->groups = 0;
+    best->chunk = default_chunk(w);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const auto t0 = std::chrono::steady_clock::now();
-    for (int gc : groups_c) {
+    ap_status st = AP_OK;
+    for (auto [lb, gc] : cands) {
         for (int64_t cc : chunks_c) {
             if (cc < 4LL * w) continue;
             std::vector<Plan> saved;
-            for (int j : idx) {
+            bool match = true;
+            for (int j : sample) {
                 saved.push_back(b->plans[j]);
                 const ap_job &jb = b->jobs[j];
-                ap_status s = plan_plot(jb.m, jb.n, jb.w, &jb.scores, gc, cc, &b->plans[j]);
-                if (s != AP_OK) return s;
+                ap_status s = plan_plot(jb.m, jb.n, jb.w, &jb.scores, gc, cc, &b->plans[j], 1, lb);
+                if (s != AP_OK) {
+                    st = s;
+                    match = false;
+                    break;
+                }
+                const Variant *v = b->plans[j].v;
+                match &= v->groups == gc && (lb == 0 || v->lane_bits == lb);
             }
-            if (b->plans[idx[0]].v->groups != (gc ? gc : b->plans[idx[0]].v->groups)) {
-                for (size_t k = 0; k < idx.size(); ++k) b->plans[idx[k]] = saved[k];
-                continue;   // no compiled variant for this request
+            if (!match) {                  // no compiled variant for this request
+                for (size_t k = 0; k < saved.size(); ++k) b->plans[sample[k]] = saved[k];
+                if (st != AP_OK) break;
+                continue;
             }
             Group g;
-            g.v = b->plans[idx[0]].v;
-            g.jobs = idx;
+            g.v = b->plans[sample[0]].v;
+            g.jobs = sample;
             cudaError_t e = upload_params(b);
             if (e == cudaSuccess) e = prepare_group(g, b->plans);
             float ms = 0;
@@ -218,7 +337,7 @@ ap_status tune_class(ap_batch *b, const std::vector<int> &idx, int nu, int w,
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             }
             if (g.d_tiles) cudaFree(g.d_tiles);
-            for (size_t k = 0; k < idx.size(); ++k) b->plans[idx[k]] = saved[k];
+            for (size_t k = 0; k < sample.size(); ++k) b->plans[sample[k]] = saved[k];
             if (e != cudaSuccess) {
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
@@ -226,14 +345,17 @@ ap_status tune_class(ap_batch *b, const std::vector<int> &idx, int nu, int w,
             }
             if (ms < best_ms) {
                 best_ms = ms;
-                *best = {gc, cc};
+                best->lane_bits = lb;
+                best->groups = gc;
+                best->chunk = cc;
             }
         }
+        if (st != AP_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *tune_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    return AP_OK;
+    return st;
 }
 
 }  // namespace
@@ -283,15 +405,14 @@ ap_status ap_batch_create(const ap_job *jobs, int32_t njobs, const ap_batch_opti
         std::map<std::tuple<int, int, int>, std::vector<int>> classes;
         for (size_t j = 0; j < b->jobs.size(); ++j)
             classes[std::make_tuple(b->plans[j].nu, b->plans[j].mu, b->plans[j].w)].push_back((int)j);
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, std::max(0, b->device));
         for (auto &kv : classes) {
-            const auto key = std::make_tuple(std::get<0>(kv.first), std::get<1>(kv.first),
-                                             std::get<2>(kv.first), sms);
-            std::pair<int, int64_t> best;
+            const int nu = std::get<0>(kv.first), mu = std::get<1>(kv.first), w = std::get<2>(kv.first);
+            const std::string key = tune_key(b->device, nu, mu, w);
+            Schedule best;
             bool cached = false;
             {
                 std::lock_guard<std::mutex> lk(g_tune_mu);
+                load_tune_cache();
                 auto it = g_tuned.find(key);
                 if (it != g_tuned.end()) {
                     best = it->second;
@@ -299,19 +420,18 @@ ap_status ap_batch_create(const ap_job *jobs, int32_t njobs, const ap_batch_opti
                 }
             }
             if (!cached) {
-                ap_status s = tune_class(b, kv.second, std::get<0>(kv.first),
-                                         std::get<2>(kv.first), &best, &b->info.tune_ms);
+                ap_status s = tune_class(b, kv.second, nu, w, &best, &b->info.tune_ms);
                 if (s != AP_OK) {
                     release(b);
                     return s;
                 }
                 std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tuned[key] = best;
+                store_tune_cache(key, best);
             }
             for (int j : kv.second) {
                 const ap_job &jb = b->jobs[j];
-                ap_status s = plan_plot(jb.m, jb.n, jb.w, &jb.scores, best.first, best.second,
-                                        &b->plans[j]);
+                ap_status s = plan_plot(jb.m, jb.n, jb.w, &jb.scores, best.groups, best.chunk,
+                                        &b->plans[j], 1, best.lane_bits);
                 if (s != AP_OK) {
                     release(b);
                     return s;

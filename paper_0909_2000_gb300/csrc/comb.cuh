@@ -93,6 +93,9 @@ struct CombParams {
     uint32_t shlo[4];
     uint32_t spread_hi, spread_lo;
     int64_t step;       // x offset between consecutive plot rows (vertical step h)
+    int32_t warp_words; // shared-memory words per warp of a plain launch
+    uint32_t scale;     // plot values are scale x the comb's values (gcd of the scores)
+    int32_t tab;        // 1: the aligned row split of the G > 1 table path fits (tabg_split_ok)
 };
 
 // ---------------------------------------------------------------------------
@@ -334,6 +337,10 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
 {
     constexpr int NS = L::NS;
     constexpr int SPW = NGRP * NS;
+    // Output words are scaled lane by lane in one multiply: every lane's
+    // product fits its lane (the output width was checked against scale x
+    // the largest value), so no carry crosses a lane.
+    const uint32_t sc = p.scale;
     if (WIDE && L::BITS == 8 && NGRP == 32 && p.out_bytes == 2 && cnt == kOB &&
         ((((uintptr_t)p.out) | (uintptr_t)(2 * p.ld)) & 15u) == 0) {
         // byte values widened to 16 bits: four threads per row (8 columns
@@ -352,7 +359,7 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
             const uint32_t sel = b | ((b + 4u) << 4);
             uint32_t o4[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) o4[k] = prmt(prmt(wv[2 * k], wv[2 * k + 1], sel), 0u, 0x4140u);
+            for (int k = 0; k < 4; ++k) o4[k] = prmt(prmt(wv[2 * k], wv[2 * k + 1], sel), 0u, 0x4140u) * sc;
             if (i < p.rows)
                 *(uint4 *)((uint16_t *)p.out + i * p.ld + jbase + 8 * part) =
                     make_uint4(o4[0], o4[1], o4[2], o4[3]);
@@ -378,7 +385,7 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 o4[k] = prmt(prmt(wv[4 * k], wv[4 * k + 1], sel), prmt(wv[4 * k + 2], wv[4 * k + 3], sel),
-                             0x5410u);
+                             0x5410u) * sc;
             if (i < p.rows)
                 *(uint4 *)((uint8_t *)p.out + i * p.ld + jbase + 16 * half) =
                     make_uint4(o4[0], o4[1], o4[2], o4[3]);
@@ -398,8 +405,8 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
             const uint32_t w0 = sp[0], w1 = sp[NGRP + 1], w2 = sp[2 * (NGRP + 1)], w3 = sp[3 * (NGRP + 1)];
             const int64_t off = i * p.ld + jbase + j4;
             if (L::BITS == 10) {                // lanes are not byte-aligned: shift out
-                const uint32_t v0 = lane_of<L>(w0, b), v1 = lane_of<L>(w1, b);
-                const uint32_t v2 = lane_of<L>(w2, b), v3 = lane_of<L>(w3, b);
+                const uint32_t v0 = lane_of<L>(w0, b) * sc, v1 = lane_of<L>(w1, b) * sc;
+                const uint32_t v2 = lane_of<L>(w2, b) * sc, v3 = lane_of<L>(w3, b) * sc;
                 if (p.out_bytes == 1) {
                     uint8_t *o = (uint8_t *)p.out + off;
                     const uint32_t word = v0 | (v1 << 8) | (v2 << 16) | (v3 << 24);
@@ -424,7 +431,7 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
             if (p.out_bytes == 1) {
                 const uint32_t sel = bb | ((bb + 4u) << 4);
                 const uint32_t lo = prmt(w0, w1, sel), hi = prmt(w2, w3, sel);
-                const uint32_t word = prmt(lo, hi, 0x5410u);
+                const uint32_t word = prmt(lo, hi, 0x5410u) * sc;
                 uint8_t *o = (uint8_t *)p.out + off;
                 if (j4 + 4 <= cnt) {
                     *(uint32_t *)o = word;
@@ -435,12 +442,12 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
                 uint32_t lo, hi;
                 if (L::BITS == 8) {
                     const uint32_t sel = bb | ((bb + 4u) << 4);
-                    lo = prmt(prmt(w0, w1, sel), 0u, 0x4140u);
-                    hi = prmt(prmt(w2, w3, sel), 0u, 0x4140u);
+                    lo = prmt(prmt(w0, w1, sel), 0u, 0x4140u) * sc;
+                    hi = prmt(prmt(w2, w3, sel), 0u, 0x4140u) * sc;
                 } else {
                     const uint32_t sel = bb | ((bb + 1u) << 4) | ((bb + 4u) << 8) | ((bb + 5u) << 12);
-                    lo = prmt(w0, w1, sel);
-                    hi = prmt(w2, w3, sel);
+                    lo = prmt(w0, w1, sel) * sc;
+                    hi = prmt(w2, w3, sel) * sc;
                 }
                 uint16_t *o = (uint16_t *)p.out + off;
                 if (j4 + 4 <= cnt) {
@@ -457,7 +464,7 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
             const int64_t i = iw + rw;
             if (i >= p.rows) break;
             if (lane < cnt) {
-                const uint32_t v = lane_of<L>(stage[lane * (NGRP + 1) + rw / NS], rw % NS);
+                const uint32_t v = lane_of<L>(stage[lane * (NGRP + 1) + rw / NS], rw % NS) * sc;
                 const int64_t off = i * p.ld + jbase + lane;
                 if (p.out_bytes == 1) ((uint8_t *)p.out)[off] = (uint8_t)v;
                 else ((uint16_t *)p.out)[off] = (uint16_t)v;
@@ -827,7 +834,7 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
 }
 
 // Shared-memory words one warp needs for a tile: the exit ring plus the
-// output stage.
+// output stage (variants with match tables add tab_words(R)).
 template <int G>
 __host__ __device__ constexpr int comb_warp_words(int ring)
 {
@@ -866,14 +873,663 @@ __device__ __forceinline__ bool tile_same_top(const CombParams &p, int64_t sg, i
     return (o & 0x80u) == 0u || (a & 0x80u) != 0u;
 }
 
+// ---------------------------------------------------------------------------
+// Match tables for small alphabets (LCS, 7-bit keys, one thread per strip
+// group)
+// ---------------------------------------------------------------------------
+//
+// A row register of thread `grp` at row k holds the strips iw + 4 grp + b
+// (b = 0..3), whose row-k characters are x[iw + 4 grp + k + b]: the four
+// characters at warp position p = 4 grp + k.  The match word of that row
+// against a y character c is a function of p and c alone, so a warp whose x
+// characters (all SPW + R + 3 of them) take at most kTabSyms distinct values
+// keeps, in shared memory, one word per (symbol, position):
+//     T[s][p] byte b = 0xFF if x[iw + p + b] == sym[s], else 0x80
+// (slot kTabSyms: every byte 0x80, for y characters absent from the warp's
+// x).  That is the "h | ~mismatch | MSB" operand of the cell: the column's
+// row masks become one 16-byte shared load per four rows, with no compare,
+// spread or row shift per column.  A y character's slot comes from a
+// 256-entry byte map.  Warps with more distinct characters take the general
+// path.
+constexpr int kTabSyms = 4;
+
+__host__ __device__ constexpr int tab_positions(int R) { return 4 * 31 + R; }
+
+// Shared words of the tables: (kTabSyms + 1) tables, the y map (256 bytes),
+// the presence bit set (8 words) and the symbols (8 bytes).
+__host__ __device__ constexpr int tab_words(int R)
+{
+    return ((kTabSyms + 1) * tab_positions(R) + 64 + 8 + 2 + 3) / 4 * 4;   // keeps 16-byte alignment
+}
+
+// Which compiled variants carry the table path.
+__host__ __device__ constexpr bool has_tables(int key_bits, int groups, int nu, bool xrows)
+{
+    return key_bits == 7 && groups == 1 && nu == 1 && !xrows;
+}
+
+#ifndef AP_TAB_CPS
+#define AP_TAB_CPS 2   // plot columns per step of the table path (2 or 4)
+#endif
+#ifndef AP_TAB_HNF
+#define AP_TAB_HNF 0   // columns of each step whose right output is formed on the FMA pipe
+#endif
+
+// Builds the warp's tables; false (warp-uniform) if the x characters of the
+// warp take more than kTabSyms values.
+template <int R>
+__device__ __forceinline__ bool build_tables(const CombParams &p, int64_t iw, uint32_t *tab,
+                                             int lane)
+{
+    constexpr int P = tab_positions(R);
+    uint32_t *tb = tab;
+    uint8_t *ymap = (uint8_t *)(tab + (kTabSyms + 1) * P);
+    uint32_t *bits = tab + (kTabSyms + 1) * P + 64;
+    uint8_t *sym = (uint8_t *)(bits + 8);
+    if (lane < 8) bits[lane] = 0u;
+    __syncwarp();
+    // every x character a row of the warp reads: positions 0 .. P + 2
+    for (int q = lane; q < P + 3; q += 32) {
+        const int64_t idx = iw + q;
+        if (idx < p.m) {
+            const uint32_t c = __ldg(p.x + idx);
+            atomicOr(&bits[c >> 5], 1u << (c & 31u));
+        }
+    }
+    __syncwarp();
+    const uint32_t wbits = (lane < 8) ? bits[lane] : 0u;
+    const int cnt = __popc(wbits);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 7);
+    if (total > kTabSyms) return false;
+    // slot of every byte value: its rank among the present characters, or
+    // kTabSyms if absent; lane l maps the bytes 8l .. 8l + 7 (word l / 4)
+    const int before = __shfl_sync(0xffffffffu, incl - cnt, lane >> 2);
+    const uint32_t wl = __shfl_sync(0xffffffffu, wbits, lane >> 2);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const uint32_t c = (uint32_t)(lane * 8 + t);
+        const uint32_t bit = c & 31u;
+        const bool present = (wl >> bit) & 1u;
+        const int rank = before + __popc(wl & ((1u << bit) - 1u));
+        ymap[c] = (uint8_t)(present ? rank : kTabSyms);
+        if (present) sym[rank] = (uint8_t)c;
+    }
+    __syncwarp();
+    for (int q = lane; q < P; q += 32) {
+        uint32_t ch[4];
+        bool in[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int64_t idx = iw + q + b;
+            in[b] = idx < p.m;
+            ch[b] = in[b] ? (uint32_t)__ldg(p.x + idx) : 0u;
+        }
+        for (int s = 0; s < total; ++s) {
+            const uint32_t c = sym[s];
+            uint32_t wv = 0u;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) wv |= ((in[b] && ch[b] == c) ? 0xFFu : 0x80u) << (8 * b);
+            tb[s * P + q] = wv;
+        }
+        tb[kTabSyms * P + q] = 0x80808080u;
+    }
+    __syncwarp();
+    return true;
+}
+
+// One comb cell with the match folded in by a table word X (0xFF in match
+// lanes, 0x80 in mismatch lanes; padding rows are masked to 0x80 by pk):
+// hc = h | (X & pk), then as in cell<U8Lanes>.  FMA_HN forms the right
+// output as (h + v) - bottom with two multiply-adds (lane sums stay below
+// 256, so no carry or borrow crosses a lane) instead of one logic
+// instruction (a compile-time constant after unrolling).
+__device__ __forceinline__ void cell_tab(uint32_t &h, uint32_t &v, uint32_t X, uint32_t pk,
+                                         uint32_t one, uint32_t neg1, bool FMA_HN)
+{
+    const uint32_t hc = h | (X & pk);
+    const uint32_t t = mad_lo(v, neg1, hc);                 // hc - v
+    const uint32_t M = prmt(t, 0u, U8Lanes::SIGNREP);
+    const uint32_t vn = (h & M) | (v & ~M);
+    if (FMA_HN) h = mad_lo(vn, neg1, mad_lo(h, one, v));
+    else h = h ^ v ^ vn;
+    v = vn;
+}
+
+// 16-byte shared-memory load at a 32-bit shared address.
+__device__ __forceinline__ uint4 lds128(uint32_t saddr)
+{
+    uint4 r;
+    asm("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "r"(saddr));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// The LCS comb of one tile through the tables (one thread per strip group,
+// 7-bit keys in 8-bit lanes).  The same method, window count and output as
+// comb_tile; CPS plot columns per step (CPS independent dependency chains per
+// thread), each column's row words read from the table of its y character.
+template <int R, int PADU, int CPS, int HNF>
+__device__ __forceinline__ void comb_tile_tab(const CombParams &p, int64_t sg, int64_t ch,
+                                              uint32_t *ring, const uint32_t *tab)
+{
+    using L = U8Lanes;
+    constexpr int NS = 4;
+    constexpr int NGRP = 32;
+    constexpr int SPW = NGRP * NS;
+    constexpr int P = tab_positions(R);
+    static_assert(R % 4 == 0, "rows in whole x words");
+    static_assert(CPS == 2 || CPS == 4, "two or four columns per step");
+    static_assert(PADU <= R, "padding window larger than the lane");
+
+    const int lane = threadIdx.x & 31;
+    const int grp = lane;
+    uint32_t *stage = ring + p.ring * NGRP;
+    const uint8_t *ymap = (const uint8_t *)(tab + (kTabSyms + 1) * P);
+
+    const int64_t iw = sg * SPW;
+    const int64_t c0 = ch * p.chunk;
+    const int64_t c1 = (c0 + p.chunk < p.cols) ? c0 + p.chunk : p.cols;
+    const int wk = p.w;
+
+    uint32_t pk[PADU > 0 ? PADU : 1];
+#pragma unroll
+    for (int t = 0; t < PADU; ++t) pk[t] = ((R - PADU + t) >= wk) ? 0x80808080u : 0xFFFFFFFFu;
+
+    for (int e = lane; e < p.ring * NGRP; e += 32) ring[e] = 0u;
+    __syncwarp();
+
+    uint32_t h[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) h[k] = 0u;
+
+    const int ncomb = (int)(c1 - c0) + wk - 1;
+    const int steps = (ncomb + CPS - 1) / CPS;
+    const uint32_t wvec = (uint32_t)wk * L::ONES;
+    const uint32_t inval_bias = (uint32_t)(128u - (uint32_t)wk) * L::ONES;
+    // renormalise every rsteps steps, by CPS * rsteps key units (p.renorm is
+    // given for two-column steps)
+    const int rsteps = (p.renorm * 2) / CPS;
+    const int kdrop = CPS * rsteps;
+    const uint32_t rr_bias = (uint32_t)(128u - (uint32_t)kdrop) * L::ONES;
+    const int ring_mask = p.ring - 1;
+    const uint32_t ring_maskv = (uint32_t)ring_mask * L::ONES;
+    const int plot_cols = (int)(c1 - c0);
+    const uint8_t *ytile = p.y + c0;
+    const int ylast = (int)(p.n - 1 - c0);
+    const uint32_t one = p.one;
+    const uint32_t neg1 = 0u - p.one;
+    const uint32_t tgrp = smem_addr(tab + 4 * grp);   // this thread's row words start here
+
+    int kc = wk;
+    int since = 0;
+    uint32_t d = 0;
+
+    uint8_t *ring8 = (uint8_t *)(ring + grp);
+    auto count_exit = [&](uint32_t ex, uint32_t knew, int col) {
+        const uint32_t age = knew - ex;
+        const uint32_t valid = ((age + inval_bias) & L::MSB ^ L::MSB) >> 7;
+        d += valid;
+        const uint32_t colb = (uint32_t)(col & ring_mask) * L::ONES;
+        const uint32_t slots = (colb + L::MSB - age) & ring_maskv;
+#pragma unroll
+        for (int b = 0; b < NS; ++b) {
+            const uint32_t slot = prmt(slots, 0u, 0x4440u | (uint32_t)b);
+            ring8[slot * (uint32_t)(NGRP * 4) + b] = (uint8_t)prmt(valid, 0u, 0x4440u | (uint32_t)b);
+        }
+    };
+    auto expire = [&](int col) {
+        uint32_t *e = ring + ((col - wk) & ring_mask) * NGRP + grp;
+        d -= *e;
+        *e = 0u;
+    };
+    auto ychar = [&](int yi) -> uint32_t {
+        yi = yi > ylast ? ylast : yi;
+        return (uint32_t)__ldg(ytile + yi);
+    };
+
+    uint32_t yc[CPS];
+#pragma unroll
+    for (int c = 0; c < CPS; ++c) yc[c] = ychar(c);
+
+    for (int s = 0; s < steps; ++s) {
+        if (s > 0) {
+            kc += CPS;
+            if (++since == rsteps) {       // Proposition 3.4: old keys collapse to 0
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const uint32_t t = mad_lo(h[k], one, rr_bias);
+                    h[k] = t & prmt(t, 0u, L::SIGNREP) & L::LOW;
+                }
+                kc = wk;
+                since = 0;
+            }
+        }
+        const uint32_t knew0 = (uint32_t)kc * L::ONES;
+        uint32_t tcol[CPS];
+        uint32_t v[CPS];
+#pragma unroll
+        for (int c = 0; c < CPS; ++c) {
+            tcol[c] = tgrp + (uint32_t)ymap[yc[c]] * (uint32_t)(4 * P);
+            v[c] = knew0 + (uint32_t)c * L::ONES;
+        }
+#pragma unroll
+        for (int c = 0; c < CPS; ++c) yc[c] = ychar(CPS * (s + 1) + c);   // next step's characters
+#pragma unroll
+        for (int j = 0; j < R / 4; ++j) {
+            uint4 X[CPS];
+#pragma unroll
+            for (int c = 0; c < CPS; ++c) X[c] = lds128(tcol[c] + 16u * (uint32_t)j);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int k = 4 * j + r;
+                const int pi = k - (R - PADU);
+                const uint32_t kp = (pi >= 0) ? pk[pi < 0 ? 0 : pi] : 0xFFFFFFFFu;
+#pragma unroll
+                for (int c = 0; c < CPS; ++c) {
+                    const uint32_t xv = r == 0 ? X[c].x : (r == 1 ? X[c].y : (r == 2 ? X[c].z : X[c].w));
+                    cell_tab(h[k], v[c], xv, kp, one, neg1, c < HNF);
+                }
+            }
+        }
+        // bottom of the strip: count exits (Theorem 3.1) and stage the plot
+#pragma unroll
+        for (int c = 0; c < CPS; ++c) {
+            const int col = CPS * s + c;
+            if (col < ncomb) {
+                expire(col);
+                count_exit(v[c], knew0 + (uint32_t)c * L::ONES, col);
+                if (col >= wk - 1) {
+                    const int jo = col - (wk - 1);
+                    const int jj = jo & (kOB - 1);
+                    stage[jj * (NGRP + 1) + grp] = wvec - d;
+                    if (jj == kOB - 1 || jo == plot_cols - 1) {
+                        __syncwarp();
+                        flush_stage<L, NGRP, false>(p, stage, iw, c0 + jo - jj, jj + 1, lane);
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+    }
+}
+
 // 8-bit-lane tiles whose characters allow it comb with the short mismatch
 // test; the rest take the general one.  Measured on the 100k DNA plot,
 // w = 100: 85.5 -> 82.5 ms.
+// ---------------------------------------------------------------------------
+// Match tables when a strip group's rows are split over G > 1 threads (LCS;
+// full 8-bit keys or 16-bit lanes)
+// ---------------------------------------------------------------------------
+//
+// Thread (grp, g) holds rows ub_g .. ub_{g+1} - 1 of the strips iw + NS grp
+// + b, so its row k reads the characters at warp position NS grp + ub_g + k.
+// The split is ub_g = floor(g w / G) rounded down to RPL rows (the rows of
+// one vector load), which keeps every load aligned; the plan uses this path
+// only where every share fits the thread's R rows with at most PADU padding
+// rows (tab_split_ok), else the even split of the general path.
+//
+// Each g has its own copy of the tables, holding positions ub_g + q: a load
+// phase of the warp (128 bytes) then covers G copies, whose bases differ by
+// 32 / G banks, and every symbol table is a whole number of 32-word rows, so
+// threads of different g, combing different columns (the wavefront is
+// skewed) and so reading different symbols' tables, still hit distinct
+// banks.  Table words: lane = all ones for a match, else 0 (full 8-bit keys)
+// or the lane's top bit (16-bit lanes): the operand the cell ORs into h.
+
+__host__ __device__ constexpr int tabg_rpl(int ns) { return ns == 4 ? 4 : (ns == 2 ? 2 : 1); }
+
+// positions per symbol table of one copy
+__host__ __device__ constexpr int tabg_q(int ns, int g, int r)
+{
+    return (ns * (32 / g - 1) + r + ns + 31) / 32 * 32;
+}
+
+// words per copy: the symbol tables, padded so that copy g starts 32 / G
+// banks after copy g - 1
+__host__ __device__ constexpr int tabg_s(int ns, int g, int r)
+{
+    return ((kTabSyms + 1) * tabg_q(ns, g, r) + 31) / 32 * 32 + 32 / g;
+}
+
+__host__ __device__ constexpr int tabg_words(int ns, int g, int r)
+{
+    return (g * tabg_s(ns, g, r) + 64 + 8 + 2 + 3) / 4 * 4;
+}
+
+__host__ __device__ constexpr bool has_tables_g(int key_bits, int groups, int nu, bool xrows)
+{
+    return nu == 1 && !xrows && groups > 1 && (key_bits == 8 || key_bits == 15);
+}
+
+// First row of thread g's share (g = G: the window w).
+__host__ __device__ inline int tabg_ub(int w, int G, int rpl, int g)
+{
+    return g >= G ? w : (g * w / G) / rpl * rpl;
+}
+
+// The aligned split fits: every share has at most R rows and at least
+// R - PADU of them are real.
+__host__ __device__ inline bool tabg_split_ok(int w, int G, int R, int rpl, int padu)
+{
+    for (int g = 0; g < G; ++g) {
+        const int n = tabg_ub(w, G, rpl, g + 1) - tabg_ub(w, G, rpl, g);
+        if (n > R || n < R - padu) return false;
+    }
+    return true;
+}
+
+template <int RPL>
+__device__ __forceinline__ void lds_rows(uint32_t saddr, uint32_t *out)
+{
+    if (RPL == 4) {
+        asm("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+            : "=r"(out[0]), "=r"(out[1]), "=r"(out[2]), "=r"(out[3]) : "r"(saddr));
+    } else if (RPL == 2) {
+        asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(out[0]), "=r"(out[1]) : "r"(saddr));
+    } else {
+        asm("ld.shared.u32 %0, [%1];" : "=r"(out[0]) : "r"(saddr));
+    }
+}
+
+// Builds the tables of a G > 1 warp; false (warp-uniform) if its x
+// characters take more than kTabSyms values.
+template <class L, int G, int R>
+__device__ __forceinline__ bool build_tables_g(const CombParams &p, int64_t iw, uint32_t *tab,
+                                               int lane)
+{
+    constexpr int NS = L::NS;
+    constexpr int RPL = tabg_rpl(NS);
+    constexpr int Q = tabg_q(NS, G, R);
+    constexpr int S = tabg_s(NS, G, R);
+    uint8_t *ymap = (uint8_t *)(tab + G * S);
+    uint32_t *bits = tab + G * S + 64;
+    uint8_t *sym = (uint8_t *)(bits + 8);
+    const int wk = p.w;
+    const int span = NS * (32 / G - 1) + wk + NS - 1;   // characters the warp's rows read
+    if (lane < 8) bits[lane] = 0u;
+    __syncwarp();
+    for (int q = lane; q < span; q += 32) {
+        const int64_t idx = iw + q;
+        if (idx < p.m) {
+            const uint32_t c = __ldg(p.x + idx);
+            atomicOr(&bits[c >> 5], 1u << (c & 31u));
+        }
+    }
+    __syncwarp();
+    const uint32_t wbits = (lane < 8) ? bits[lane] : 0u;
+    const int cnt = __popc(wbits);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 7);
+    if (total > kTabSyms) return false;
+    const int before = __shfl_sync(0xffffffffu, incl - cnt, lane >> 2);
+    const uint32_t wl = __shfl_sync(0xffffffffu, wbits, lane >> 2);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const uint32_t c = (uint32_t)(lane * 8 + t);
+        const uint32_t bit = c & 31u;
+        const bool present = (wl >> bit) & 1u;
+        const int rank = before + __popc(wl & ((1u << bit) - 1u));
+        ymap[c] = (uint8_t)(present ? rank : kTabSyms);
+        if (present) sym[rank] = (uint8_t)c;
+    }
+    __syncwarp();
+    const uint32_t nomatch = L::FULL ? 0u : L::MSB;
+    for (int g = 0; g < G; ++g) {
+        const int ub = tabg_ub(wk, G, RPL, g);
+        uint32_t *copy = tab + g * S;
+        for (int q = lane; q < Q; q += 32) {
+            uint32_t ch[NS];
+            bool in[NS];
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                const int64_t idx = iw + ub + q + b;
+                in[b] = idx < p.m;
+                ch[b] = in[b] ? (uint32_t)__ldg(p.x + idx) : 0u;
+            }
+            for (int s = 0; s < total; ++s) {
+                const uint32_t c = sym[s];
+                uint32_t wv = nomatch;
+#pragma unroll
+                for (int b = 0; b < NS; ++b)
+                    if (in[b] && ch[b] == c) wv |= L::MASK << (L::BITS * b);
+                copy[s * Q + q] = wv;
+            }
+            copy[kTabSyms * Q + q] = nomatch;
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// One comb cell with the match folded in by a table word (see above; X & pk
+// is the no-match word in padding rows).
+template <class L>
+__device__ __forceinline__ void cell_tx(uint32_t &h, uint32_t &v, uint32_t X, uint32_t pk,
+                                        uint32_t neg1, uint32_t sph, uint32_t spl)
+{
+    uint32_t M;
+    if (L::FULL) {
+        const uint32_t hm = h | (X & pk);
+        M = prmt(ge_lanes<L>(hm, v, neg1), 0u, L::SIGNREP);
+    } else {
+        const uint32_t hc = h | (X & pk);
+        const uint32_t t = mad_lo(v, neg1, hc);
+        M = spread<L>(t, sph, spl);
+    }
+    const uint32_t vn = (h & M) | (v & ~M);
+    h = h ^ v ^ vn;
+    v = vn;
+}
+
+// The LCS comb of one tile through per-g tables, rows split over G > 1
+// threads with the skewed wavefront of comb_tile: the same method, window
+// count and output; only the row masks come from the tables and the split
+// is the aligned one.
+template <class L, int R, int G, int PADU>
+__device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, int64_t ch,
+                                               uint32_t *ring, const uint32_t *tab)
+{
+    constexpr int NS = L::NS;
+    constexpr int NGRP = 32 / G;
+    constexpr int SPW = NGRP * NS;
+    constexpr int RPL = tabg_rpl(NS);
+    constexpr int Q = tabg_q(NS, G, R);
+    constexpr int S = tabg_s(NS, G, R);
+    static_assert(G > 1 && R % RPL == 0, "rows in whole loads");
+    static_assert(PADU <= R, "padding window larger than the lane");
+
+    const int lane = threadIdx.x & 31;
+    const int g = lane % G;
+    const int grp = lane / G;
+    uint32_t *stage = ring + p.ring * NGRP;
+    const uint8_t *ymap = (const uint8_t *)(tab + G * S);
+
+    const int64_t iw = sg * SPW;
+    const int64_t c0 = ch * p.chunk;
+    const int64_t c1 = (c0 + p.chunk < p.cols) ? c0 + p.chunk : p.cols;
+    const int wk = p.w;
+    const int nreal = tabg_ub(wk, G, RPL, g + 1) - tabg_ub(wk, G, RPL, g);
+
+    const uint32_t nomatch = L::FULL ? 0u : L::MSB;
+    uint32_t pk[PADU > 0 ? PADU : 1];
+#pragma unroll
+    for (int t = 0; t < PADU; ++t) pk[t] = ((R - PADU + t) >= nreal) ? nomatch : 0xFFFFFFFFu;
+
+    for (int e = lane; e < p.ring * NGRP; e += 32) ring[e] = 0u;
+    __syncwarp();
+
+    uint32_t h[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) h[k] = 0u;
+
+    const int ncomb = (int)(c1 - c0) + wk - 1;
+    const int nunits = (ncomb + 1) / 2;
+    const int steps = nunits + G - 1;
+    const uint32_t wvec = (uint32_t)wk * L::ONES;
+    const uint32_t inval_bias = (uint32_t)((1u << (L::BITS - 1)) - (uint32_t)wk) * L::ONES;
+    const int kdrop = 2 * p.renorm;
+    const uint32_t rr_bias = (uint32_t)((1u << (L::BITS - 1)) - (uint32_t)kdrop) * L::ONES;
+    const uint32_t rrv = (uint32_t)kdrop * L::ONES;
+    const uint32_t wkv = (uint32_t)wk * L::ONES;
+    const int ring_mask = p.ring - 1;
+    const uint32_t ring_maskv = (uint32_t)ring_mask * L::ONES;
+    const int plot_cols = (int)(c1 - c0);
+    const uint8_t *ytile = p.y + c0;
+    const int ylast = (int)(p.n - 1 - c0);
+    const uint32_t one = p.one;
+    const uint32_t neg1 = 0u - p.one;
+    const uint32_t sph = p.spread_hi, spl = p.spread_lo;
+    const uint32_t tbase = smem_addr(tab + g * S + NS * grp);   // this thread's row 0, symbol 0
+
+    int kc = wk;
+    int since = 0;
+    uint32_t d = 0;
+    uint32_t vdown[2] = {0u, 0u};
+
+    uint8_t *ring8 = (uint8_t *)(ring + grp);
+    auto count_exit = [&](uint32_t ex, uint32_t knew, int col) {
+        const uint32_t age = knew - ex;
+        const uint32_t inval = (L::FULL ? ge_lanes<L>(age, wkv, neg1) : age + inval_bias) & L::MSB;
+        const uint32_t valid = (inval ^ L::MSB) >> (L::BITS - 1);
+        d += valid;
+        if (L::BITS == 8) {
+            const uint32_t colb = (uint32_t)(col & ring_mask) * L::ONES;
+            const uint32_t slots = L::FULL ? sub_lanes<L>(colb, age) : (colb + L::MSB - age) & ring_maskv;
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                const uint32_t slot = prmt(slots, 0u, 0x4440u | (uint32_t)b);
+                ring8[slot * (uint32_t)(NGRP * 4) + b] = (uint8_t)prmt(valid, 0u, 0x4440u | (uint32_t)b);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                if ((valid >> (L::BITS * b)) & 1u) {
+                    const int a = (int)((age >> (L::BITS * b)) & L::MASK);
+                    uint32_t *e = ring + ((col - a) & ring_mask) * NGRP + grp;
+                    *e += 1u << (L::BITS * b);
+                }
+            }
+        }
+    };
+    auto expire = [&](int col) {
+        if (L::BITS == 8 || col >= wk) {
+            uint32_t *e = ring + ((col - wk) & ring_mask) * NGRP + grp;
+            d -= *e;
+            *e = 0u;
+        }
+    };
+    auto stage_and_flush = [&](int col, bool bottom) {
+        if (col >= wk - 1 && col < ncomb) {
+            const int jo = col - (wk - 1);
+            const int jj = jo & (kOB - 1);
+            if (bottom) stage[jj * (NGRP + 1) + grp] = wvec - d;
+            if (jj == kOB - 1 || jo == plot_cols - 1) {
+                __syncwarp();
+                flush_stage<L, NGRP, false>(p, stage, iw, c0 + jo - jj, jj + 1, lane);
+                __syncwarp();
+            }
+        }
+    };
+    auto ychar = [&](int yi) -> uint32_t {
+        yi = yi < 0 ? 0 : (yi > ylast ? ylast : yi);
+        return (uint32_t)__ldg(ytile + yi);
+    };
+
+    for (int s = 0; s < steps; ++s) {
+        const int u = s - g;
+        if (u > 0) {
+            kc += 2;
+            if (++since == p.renorm) {     // Proposition 3.4: old keys collapse to 0
+#pragma unroll
+                for (int k = 0; k < R; ++k) h[k] = renorm_key<L>(h[k], rr_bias, rrv, one, neg1, sph, spl);
+                kc = wk;
+                since = 0;
+            }
+        }
+        const uint32_t knew0 = (uint32_t)kc * L::ONES;
+        const uint32_t knew1 = knew0 + L::ONES;
+        const uint32_t in0 = __shfl_up_sync(0xffffffffu, vdown[0], 1);
+        const uint32_t in1 = __shfl_up_sync(0xffffffffu, vdown[1], 1);
+        uint32_t va = (g == 0) ? knew0 : in0;
+        uint32_t vb = (g == 0) ? knew1 : in1;
+        const uint32_t t0 = tbase + (uint32_t)ymap[ychar(2 * u)] * (uint32_t)(4 * Q);
+        const uint32_t t1 = tbase + (uint32_t)ymap[ychar(2 * u + 1)] * (uint32_t)(4 * Q);
+#pragma unroll
+        for (int j = 0; j < R / RPL; ++j) {
+            uint32_t X0[RPL], X1[RPL];
+            lds_rows<RPL>(t0 + 4u * (uint32_t)(RPL * j), X0);
+            lds_rows<RPL>(t1 + 4u * (uint32_t)(RPL * j), X1);
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int k = RPL * j + r;
+                const int pi = k - (R - PADU);
+                const uint32_t kp = (pi >= 0) ? pk[pi < 0 ? 0 : pi] : 0xFFFFFFFFu;
+                cell_tx<L>(h[k], va, X0[r], kp, neg1, sph, spl);
+                cell_tx<L>(h[k], vb, X1[r], kp, neg1, sph, spl);
+            }
+        }
+        vdown[0] = va;
+        vdown[1] = vb;
+
+        // ---- bottom threads: count exits (Theorem 3.1) and stage the plot ----
+        const int ubot = s - (G - 1);
+        const bool bottom = (g == G - 1) && u >= 0 && u < nunits;
+        const int col0 = 2 * ubot, col1 = 2 * ubot + 1;
+        if (bottom) {
+            expire(col0);
+            count_exit(vdown[0], knew0, col0);
+        }
+        if (ubot >= 0) stage_and_flush(col0, bottom);
+        if (bottom && col1 < ncomb) {
+            expire(col1);
+            count_exit(vdown[1], knew1, col1);
+        }
+        if (ubot >= 0) stage_and_flush(col1, bottom && col1 < ncomb);
+    }
+}
+
+// Variants with match tables (LCS: 7-bit keys on one thread per strip
+// group; full 8-bit keys or 16-bit lanes on G > 1 threads, where the plan
+// allows the aligned split) first try them: warps whose x characters take
+// at most kTabSyms values comb through the tables.
 template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
 __device__ __forceinline__ void comb_tile_dispatch(const CombParams &p, int64_t sg, int64_t ch,
                                                    uint32_t *ring)
 {
     constexpr bool FAST_OK = L::BITS == 8;
+    constexpr bool TAB = L::BITS == 8 && !L::FULL && has_tables(7, G, NU, XR);
+    constexpr bool TABG = has_tables_g(L::BITS == 16 ? 15 : (L::FULL ? 8 : 0), G, NU, XR);
+    if constexpr (TAB) {
+        uint32_t *tab = ring + p.ring * (32 / G) + kOB * (32 / G + 1);
+        if (build_tables<R>(p, sg * 128, tab, threadIdx.x & 31)) {
+            comb_tile_tab<R, PADU, AP_TAB_CPS, AP_TAB_HNF>(p, sg, ch, ring, tab);
+            return;
+        }
+    }
+    if constexpr (TABG) {
+        uint32_t *tab = ring + p.ring * (32 / G) + kOB * (32 / G + 1);
+        if (p.tab && build_tables_g<L, G, R>(p, sg * (32 / G) * L::NS, tab, threadIdx.x & 31)) {
+            comb_tile_tabg<L, R, G, PADU>(p, sg, ch, ring, tab);
+            return;
+        }
+    }
     if (FAST_OK && tile_same_top<L, G>(p, sg, ch))
         comb_tile<L, R, G, NU, MU, PADU, XR, FAST_OK>(p, sg, ch, ring);
     else
@@ -885,12 +1541,12 @@ template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, AP_MIN_BLOCKS)
 comb_kernel(CombParams p)
 {
-    extern __shared__ uint32_t smem[];
+    extern __shared__ __align__(16) uint32_t smem[];
     const int wid = threadIdx.x >> 5;
     const int64_t tile = p.tile0 + (int64_t)blockIdx.x * kWarpsPerBlock + wid;
     if (tile >= p.ntiles) return;
     comb_tile_dispatch<L, R, G, NU, MU, PADU, XR>(p, tile % p.nsg, tile / p.nsg,
-                                                 smem + wid * comb_warp_words<G>(p.ring));
+                                                 smem + wid * p.warp_words);
 }
 
 // One tile of a batch: which job, and which strip group and column chunk.
@@ -916,7 +1572,7 @@ template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, AP_MIN_BLOCKS)
 comb_batch_kernel(BatchParams b)
 {
-    extern __shared__ uint32_t smem[];
+    extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     uint32_t *wsm = smem + wid * b.warp_words;

@@ -35,7 +35,7 @@ int next_pow2(int v)
 }  // namespace
 
 bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *pl,
-                    std::string *why)
+                    std::string *why, int want_lane_bits)
 {
     const bool score = nu > 1;
     const int xrows = step > 1 ? 1 : 0;
@@ -60,7 +60,22 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
             if (rows_for(4, 2, 2, 32)) rows *= 2;
         }
     } else if (!score) {
-        if (w <= 120) {
+        // A lane-format request (8, 10 or 16 bits) is honoured where that
+        // format covers w: 8-bit lanes up to 254, 10-bit lanes for 257..480,
+        // 16-bit lanes always; otherwise the default below.
+        const bool want16 = want_lane_bits == 16 && w <= 512;
+        const bool want10 = want_lane_bits == 10 && w > 256 && w <= 480;
+        if (want16) {
+            kbits = 15;
+            if (want_groups == 2 || want_groups == 4 || want_groups == 8)
+                rows_for(want_groups, 8, 16, 64);
+            if (!rows)
+                for (int g : {2, 4, 8})
+                    if (rows_for(g, 8, 16, 64)) break;
+        } else if (want10) {
+            kbits = 9;
+            if (want_groups == 8 || !rows_for(4, 3, 66, 96)) rows_for(8, 3, 33, 60);
+        } else if (w <= 120) {
             kbits = 7;
             if (want_groups == 2) rows_for(2, 4, 16, 60);
             else if (want_groups == 4) rows_for(4, 4, 8, 32);
@@ -99,13 +114,13 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
         }
     } else {
         // {3 or 4, mu, 0}: 8-bit lanes while nu * w stays below 256 (w <= 32),
-        // then 16-bit lanes on 8 threads.
+        // then 16-bit lanes on 8 threads (w <= 256).
         if (w <= 32) {
             kbits = 7;
             if (rows_for(1, 8, 8, 32)) rows *= nu;
         } else {
             kbits = 15;
-            if (rows_for(8, 4, 4, 16)) rows *= nu;
+            if (rows_for(8, 4, 4, 32)) rows *= nu;
         }
     }
     const Variant *v = (rows > 0) ? find_variant(kbits, rows, groups, nu, mu, xrows) : nullptr;
@@ -148,8 +163,11 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
     const int nlanes = v->lane_bits == 8 ? 4 : (v->lane_bits == 10 ? 3 : 2);
     pl->strips_per_warp = (32 / v->groups) * nlanes;
     const int ngrp = 32 / v->groups;
-    pl->smem = (size_t)kWarpsPerBlock * (size_t)(pl->ring * ngrp + kOB * (ngrp + 1)) * 4u;
     pl->warp_words = pl->ring * ngrp + kOB * (ngrp + 1);
+    if (has_tables(v->key_bits, v->groups, v->nu, v->xrows != 0)) pl->warp_words += tab_words(v->rows);
+    if (has_tables_g(v->key_bits, v->groups, v->nu, v->xrows != 0))
+        pl->warp_words += tabg_words(v->lane_bits == 8 ? 4 : 2, v->groups, v->rows);
+    pl->smem = (size_t)kWarpsPerBlock * (size_t)pl->warp_words * 4u;
     return true;
 }
 
@@ -265,6 +283,11 @@ void fill_params(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y, 
     p->spread_hi = 1u << 23;
     p->spread_lo = 0x3FFu;
     p->step = pl.step;
+    p->warp_words = pl.warp_words;
+    p->scale = (uint32_t)pl.scale;
+    const Variant *v = pl.v;
+    p->tab = has_tables_g(v->key_bits, v->groups, v->nu, v->xrows != 0) &&
+             tabg_split_ok(pl.w, v->groups, v->rows, tabg_rpl(v->lane_bits == 8 ? 4 : 2), v->padu);
 }
 
 cudaError_t raise_smem_limit(const void *fn)
@@ -277,7 +300,7 @@ cudaError_t raise_smem_limit(const void *fn)
     std::lock_guard<std::mutex> lk(mu);
     for (auto &d : done)
         if (d.first == fn && d.second == dev) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess) done.emplace_back(fn, dev);
     return e;
 }

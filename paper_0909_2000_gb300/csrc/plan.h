@@ -21,14 +21,17 @@ struct Plan {
     int64_t chunk = 0, nchunks = 0, nsg = 0, ntiles = 0;
     size_t smem = 0;      // dynamic shared memory per block
     int warp_words = 0;   // shared-memory words per warp
-    int max_value = 0;    // largest plot value: nu * w
+    int max_value = 0;    // largest plot value: match * w = scale * nu * w
+    int scale = 1;        // plot = scale x the combed (gcd-reduced) scheme's plot
 };
 
 // Picks the variant for window w and score blow-up {nu, mu, 0}.  `groups` > 0
 // asks for that many threads per strip group (when a variant exists).
 // Returns false (with a message) when no compiled variant covers the request.
+// `lane_bits` > 0 asks for that lane format (8, 10 or 16 bits, LCS) where it
+// covers the window.
 bool choose_variant(int w, int nu, int mu, int groups, int64_t step, Plan *pl,
-                    std::string *why);
+                    std::string *why, int lane_bits = 0);
 
 // Tiles a rows x cols plot for the chosen variant.  `chunk_hint` > 0 forces
 // the column chunk (rounded up to a multiple of 32).

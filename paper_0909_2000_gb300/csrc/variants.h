@@ -18,6 +18,7 @@ struct Variant {
     int groups;      // G: threads per strip group
     int nu, mu;      // score blow-up {nu, mu, 0}; nu = 1 is LCS
     int xrows;       // 1: vertical-step layout (one x word per unit)
+    int padu;        // trailing units of each thread that may be padding
     comb_fn_t fn;
     batch_fn_t batch_fn;
 };
@@ -29,5 +30,5 @@ const Variant *variant_table(int *count);
 
 // Instantiation helper: one template instance plus its registry entry.
 #define AP_VARIANT(LANES, KEYBITS, BITS, R, G, NU, MU, PADU, XR)                    \
-    { KEYBITS, BITS, R, G, NU, MU, XR, &ap::comb_kernel<ap::LANES, R, G, NU, MU, PADU, XR>, \
+    { KEYBITS, BITS, R, G, NU, MU, XR, PADU, &ap::comb_kernel<ap::LANES, R, G, NU, MU, PADU, XR>, \
       &ap::comb_batch_kernel<ap::LANES, R, G, NU, MU, PADU, XR> }

@@ -47,10 +47,10 @@ def test_host_side_validation_without_gpu():
         ap.plot_plan(100, 100, 10, (5, 1, 0))
     assert e.value.status == ap.AP_E_UNSUPPORTED
     with pytest.raises(ap.ApError) as e:
-        ap.plot_plan(100, 100, 10, (2, 0, 0))      # 2 x LCS: not built
+        ap.plot_plan(100, 100, 10, (10, 3, 0))     # reduced form {10,3,0}: not built
     assert e.value.status == ap.AP_E_UNSUPPORTED
     with pytest.raises(ap.ApError) as e:
-        ap.plot_plan(1000, 1000, 129, (3, 1, 0))   # beyond the compiled windows
+        ap.plot_plan(1000, 1000, 257, (3, 1, 0))   # beyond the compiled windows
     assert e.value.status == ap.AP_E_UNSUPPORTED
     with pytest.raises(ap.ApError) as e:
         ap.plot_plan(100, 100, 10, (1, 1, 0))     # not normalised
@@ -91,13 +91,29 @@ def test_every_supported_window_has_a_variant(w, scores):
     assert pl["physical_cells"] >= pl["logical_cells"] * (4 if scores == ap.SCORE else 1)
 
 
-@pytest.mark.parametrize("nu,mu", [(3, 1), (3, 2), (4, 1), (4, 2), (4, 3)])
-@pytest.mark.parametrize("w", [1, 7, 32, 33, 64, 128])
+@pytest.mark.parametrize("nu,mu", [(3, 1), (3, 2), (4, 1), (4, 2), (4, 3), (2, 0), (7, 0), (6, 3), (6, 2),
+                                   (8, 6), (12, 3)])
+@pytest.mark.parametrize("w", [1, 7, 32, 33, 64, 128, 200, 256])
 def test_blown_up_score_schemes_have_variants(nu, mu, w):
+    """Schemes reduce by g = gcd(match, mismatch); the reduced blow-up is
+    combed, so the comb height is (match / g) * w."""
+    import math
+    g = math.gcd(nu, mu)
+    rn = nu // g
+    if rn == 1 and w > 512 or rn == 2 and w > 256:
+        return
     pl = ap.plot_plan(w + 500, w + 300, w, (nu, mu, 0))
-    assert pl["comb_rows"] == nu * w
-    assert pl["rows_per_lane"] * pl["lanes_per_strip"] >= nu * w
-    assert pl["physical_cells"] >= pl["logical_cells"] * nu * nu
+    assert pl["comb_rows"] == rn * w
+    assert pl["rows_per_lane"] * pl["lanes_per_strip"] >= rn * w
+    assert pl["physical_cells"] >= pl["logical_cells"] * rn * rn
+
+
+def test_scores_whose_plot_exceeds_16_bits_are_refused():
+    import ctypes
+    sc = ap._scores((1000, 0, 0))          # 1000 x LCS: values up to 100,000
+    with pytest.raises(ap.ApError) as e:
+        ap._check(ap.load().ap_alignment_plot(None, 1000, None, 1000, 100, ctypes.byref(sc), None, 2, 900, None))
+    assert e.value.status == ap.AP_E_INVAL
 
 
 def test_plan_of_the_100k_plot():

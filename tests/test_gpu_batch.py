@@ -92,3 +92,44 @@ def test_batch_validation_names_the_bad_job(cuda_lib):
     with pytest.raises(ap.ApError) as e:
         ap.Batch([(x, y, 20, (1, 0, 0), good), (x, y, 20, (1, 0, 0), small[:, :100])])
     assert e.value.status == ap.AP_E_INVAL and "job 1" in str(e.value)
+
+
+TUNE_SCRIPT = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import torch
+import paper_0909_2000_gb300 as ap
+from paper_0909_2000_gb300 import synth
+keep, outs = [], []
+for k, (w, sc) in enumerate([(16, (1, 0, 0)), (64, (1, 0, 0)), (128, (1, 0, 0)), (40, (2, 1, 0))] * 3):
+    x = torch.from_numpy(synth.dna(k, 1, 2500 + 97 * k)).cuda()
+    y = torch.from_numpy(synth.dna(k, 2, 3000 + 53 * k)).cuda()
+    out = ap.empty_plot(x.numel() - w, y.numel() - w, torch.int16, "cuda")
+    keep.append((x, y, w, sc, out))
+    outs.append(out)
+b = ap.Batch(keep, autotune=True)
+b.run()
+torch.cuda.synchronize()
+print(json.dumps({"tune_ms": b.info()["tune_ms"], "sums": [int(o.to(torch.int64).sum()) for o in outs]}))
+"""
+
+
+def test_autotune_cache_persists_across_processes(cuda_lib, tmp_path):
+    """The tuner's choices are kept in the cache file (AP_TUNE_CACHE): a second
+    process on the same GPU kind tunes nothing and writes the same plots."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, AP_TUNE_CACHE=str(tmp_path / "tune.txt"))
+    runs = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", TUNE_SCRIPT, root], env=env, capture_output=True,
+                           text=True, timeout=900)
+        assert r.returncode == 0, r.stderr[-2000:]
+        runs.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    assert runs[0]["tune_ms"] > 0 and runs[1]["tune_ms"] == 0
+    assert runs[0]["sums"] == runs[1]["sums"]
+    lines = (tmp_path / "tune.txt").read_text().splitlines()
+    assert len(lines) == 4 and all("|" in l for l in lines)      # one per window class

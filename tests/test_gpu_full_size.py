@@ -1,16 +1,22 @@
-"""The three large workloads at full size, in the launch configuration the
+"""The large workloads at full size, in the launch configuration the
 benchmark times (needs a GPU; device memory up to ~150 GB).
 
-The oracle computes each sampled plot value on its own (the O(w^2) DP of
-Section 2 per window pair).  Properties that hold at any size are checked on
-the whole plot:
+Every value of every plot is checked against the oracle through the whole
+plot's digest (checksum and value histogram, the GPU's checksum kernel
+against the digest that tests/golden/make_golden.py stored from the oracle:
+the dynamic programme and the bit-parallel reference where both finish on
+the host, the bit-parallel reference alone for the largest plots).  The
+oracle also computes seeded plot values on its own (the O(w^2) dynamic
+programme of Section 2 per window pair).  Properties that hold at any size
+are checked on the whole plot:
 * the value range;
 * the neighbour bounds;
-* the dot list against the plot;
-* the checksum kernel's histogram against a direct count.
+* the dot list against the plot.
 
 Those whole-plot checks use torch reductions on the device; they verify the
 output and are not part of the product path."""
+import os
+
 import numpy as np
 import pytest
 
@@ -71,13 +77,18 @@ def _dots_match_plot(plot, dots, count, thr):
     assert off == count
 
 
-def _histogram_matches(ap, plot, nbins):
-    _, hist = ap.plot_checksum(plot, nbins)
-    want = torch.zeros(nbins, dtype=torch.int64, device=plot.device)
-    for r0 in range(0, plot.shape[0], BAND):
-        b = plot[r0:r0 + BAND].to(torch.int64)
-        want += torch.bincount(b.reshape(-1), minlength=nbins)[:nbins]
-    assert np.array_equal(hist, want.cpu().numpy())
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _digest_matches_golden(ap, plot, name, nbins):
+    """The GPU checksum kernel's digest of the whole plot equals the
+    oracle's stored digest (written from the oracle only)."""
+    kv = dict(l.split("=", 1) for l in open(os.path.join(GOLDEN, name + ".txt")).read().split() if "=" in l)
+    assert tuple(plot.shape) == tuple(int(v) for v in kv["shape"].split("x"))
+    cs, hist = ap.plot_checksum(plot, nbins)
+    want_hist = [int(v) for v in kv["histogram"].split(",")]
+    assert list(hist) == want_hist, "histogram differs from the oracle's"
+    assert cs == int(kv["checksum"]), "checksum differs from the oracle's"
 
 
 def test_lcs_dna_100k_w100(cuda_lib):
@@ -110,7 +121,7 @@ def test_lcs_dna_100k_w100(cuda_lib):
     # the banded plot-free path gives the same dots
     dots2, count2 = ap.alignment_dots(x, y, c.w, c.threshold)
     assert count2 == count and torch.equal(dots2[:count2], dots[:count])
-    _histogram_matches(ap, plot, c.w + 1)
+    _digest_matches_golden(ap, plot, c.name, c.w + 1)
     del plot, dots, dots2
     torch.cuda.empty_cache()
 
@@ -129,7 +140,34 @@ def test_score_protein_20k_w64(cuda_lib):
     _sampled(plot, c, 100_000, seed=22)
     # every window pair scores at least w (align position by position)
     _neighbour_bounds(plot, c.w, 2 * c.w, 2)
-    _histogram_matches(ap, plot, 2 * c.w + 1)
+    _digest_matches_golden(ap, plot, c.name, 2 * c.w + 1)
+    del plot
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("gen", [synth.dna_plot_20k, synth.dna_plot_20k_w256, synth.dna_score_80k_step5])
+def test_more_whole_plots_against_stored_oracle_digests(cuda_lib, gen):
+    """The 20k DNA plots at w = 100 (7-bit keys) and w = 256 (16-bit lanes,
+    uint16 plot), and the shape of the paper's Table 1 runs (80k x 80k,
+    {2,1,0}, w = 100, vertical step 5): whole-plot digests and samples."""
+    ap = cuda_lib
+    c = gen(0)
+    dev = torch.device("cuda")
+    x, y = torch.from_numpy(c.x).to(dev), torch.from_numpy(c.y).to(dev)
+    rows, cols = oracle.step_shape(len(c.x), len(c.y), c.w, c.step)
+    nb = c.scores[0] * c.w + 1
+    plot = ap.empty_plot(rows, cols, torch.uint8 if nb <= 256 else torch.int16, dev)
+    if c.step > 1:
+        ap.alignment_plot_step(x, y, c.w, c.step, (c.scores[0], c.scores[1], 0), out=plot)
+    else:
+        ap.alignment_plot(x, y, c.w, (c.scores[0], c.scores[1], 0), out=plot)
+    torch.cuda.synchronize()
+    _digest_matches_golden(ap, plot, c.name, nb)
+    ii = synth.below(24, 1, 20_000, rows)
+    jj = synth.below(24, 2, 20_000, cols)
+    got = plot[torch.from_numpy(ii).to(dev), torch.from_numpy(jj).to(dev)].cpu().numpy().astype(np.int64)
+    want = oracle.samples(c.x, c.y, c.w, ii * c.step, jj, c.scores[0], c.scores[1])
+    assert np.array_equal(got & 0xFFFF, want)
     del plot
     torch.cuda.empty_cache()
 

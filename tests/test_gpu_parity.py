@@ -108,6 +108,34 @@ def test_blown_up_score_schemes(cuda_lib, m, n, w, scores):
     assert g.shape == o.shape and np.array_equal(g, o), np.argwhere(g != o)[:4].tolist()
 
 
+# Schemes with a common factor g: the reduced scheme is combed and the plot
+# scaled by g as it is written; and the reduced blow-ups {3,x,0}, {4,x,0} above
+# w = 128 (16-bit lanes, up to 32 units per thread).
+SCALED_CASES = [
+    (300, 280, 40, (2, 0, 0)), (260, 300, 100, (3, 0, 0)), (300, 330, 50, (4, 2, 0)),
+    (320, 300, 60, (6, 3, 0)), (400, 420, 40, (6, 2, 0)), (500, 520, 200, (3, 1, 0)),
+    (560, 600, 256, (4, 3, 0)), (420, 440, 150, (8, 6, 0)), (200, 210, 20, (4, 2, 0)),
+    (300, 310, 120, (2, 0, 0)), (450, 470, 300, (2, 0, 0)), (330, 300, 90, (9, 3, 0)),
+]
+
+
+@pytest.mark.parametrize("m,n,w,scores", SCALED_CASES)
+def test_scaled_and_wide_score_schemes(cuda_lib, m, n, w, scores):
+    ap = cuda_lib
+    seed = m + 5 * n + w + 11 * scores[0] + scores[1]
+    x = synth.dna(seed, 1, m)
+    y, _ = synth.plant(x, synth.dna(seed, 2, n), 1, min(m, n) // 3, seed, 5, synth.DNA, 0.1, 0.05)
+    o = oracle.plot(x, y, w, scores[0], scores[1])
+    for dt in ((torch.uint8, torch.int16) if scores[0] * w <= 255 else (torch.int16,)):
+        g = gpu_plot(ap, x, y, w, scores, dt) & 0xFFFF
+        assert g.shape == o.shape and np.array_equal(g, o), (dt, np.argwhere(g != o)[:4].tolist())
+    # dots of the scaled plot: thresholds apply to the scaled values
+    thr = int(o.max()) - scores[0]
+    dots, count = ap.alignment_dots(dev(x), dev(y), w, thr, scores)
+    want = oracle.dots(o, thr)
+    assert count == len(want) and np.array_equal(ap.dots_to_numpy(dots, count), want)
+
+
 @pytest.mark.parametrize("w,scores", [(9, (1, 0, 0)), (100, (1, 0, 0)), (150, (1, 0, 0)),
                                       (300, (1, 0, 0)), (20, (2, 1, 0)), (90, (2, 1, 0)),
                                       (140, (2, 1, 0))])
