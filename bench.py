@@ -936,14 +936,22 @@ def measure_e2e(ap, c, scores, thr, dev, steps, dist=None, world=1, dev_dots=Non
     # every rank goes on only if all could pin their buffers (no rank waits alone)
     if -max_over_ranks(-ok, dist, dev) < 1.0:
         return None
-    out, dots, count = ap.alignment_plot_host(hx, hy, w, scores, out=hout, threshold=thr)   # warm-up
+    cap = 1 << 22
+    dbuf = torch.empty((cap, 3), dtype=torch.int32, pin_memory=True)
+    ws = torch.empty(ap.plot_host_workspace_size(m, n, w, scores, hout.element_size(), cap),
+                     dtype=torch.uint8, device=dev)
+
+    def call():
+        return ap.alignment_plot_host(hx, hy, w, scores, out=hout, threshold=thr, dots_cap=cap,
+                                      workspace=ws, dots_buf=dbuf)
+    out, dots, count = call()   # warm-up
     ts = []
     for _ in range(steps):
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
         t0 = time.perf_counter()
-        out, dots, count = ap.alignment_plot_host(hx, hy, w, scores, out=hout, threshold=thr)
+        out, dots, count = call()
         ts.append(max_over_ranks((time.perf_counter() - t0) * 1e3, dist, dev) / 1e3)
     t = statistics.median(ts)
     ii, jj = synth.below(17, 1, 2000, rows), synth.below(17, 2, 2000, cols)

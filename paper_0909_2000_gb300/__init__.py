@@ -273,13 +273,16 @@ def alignment_plot_step(x, y, w: int, step: int, scores=LCS, out=None, out_dtype
 
 
 def alignment_plot_host(x, y, w: int, scores=LCS, out=None, threshold=None,
-                        dots_cap: int = 1 << 22, workspace=None, stream=None):
+                        dots_cap: int = 1 << 22, workspace=None, stream=None, dots_buf=None):
     """Plot into host memory end to end (ap_alignment_plot_host).
 
     x, y: host uint8 arrays or CPU tensors (pinned copies fastest); ``out``: a
     CPU uint8/16-bit tensor of at least (m-w, n-w), row-major, ideally pinned.
     With a threshold, also returns the dots ((k, 3) int64 numpy array) and
-    their count.  Returns (out, dots, count)."""
+    their count.  ``dots_buf``: an optional reusable host buffer for the raw
+    dot records, a contiguous CPU int32 tensor of shape (dots_cap, 3)
+    (pinned copies fastest); otherwise one is allocated per call.  Returns
+    (out, dots, count)."""
     import numpy as np
     import torch
     xt = torch.as_tensor(np.ascontiguousarray(x, dtype=np.uint8) if not isinstance(x, torch.Tensor) else x)
@@ -297,7 +300,13 @@ def alignment_plot_host(x, y, w: int, scores=LCS, out=None, threshold=None,
                                            ctypes.byref(need)))
     if workspace is None:
         workspace = torch.empty(max(need.value, 1), dtype=torch.uint8, device="cuda")
-    dbuf = np.empty((max(cap, 1), 3), dtype=np.uint32)   # the library fills the first count rows
+    if dots_buf is not None:
+        if (dots_buf.dtype != torch.int32 or dots_buf.dim() != 2 or dots_buf.shape[1] != 3
+                or dots_buf.is_cuda or not dots_buf.is_contiguous() or dots_buf.shape[0] < max(cap, 1)):
+            raise ValueError("dots_buf must be a contiguous CPU int32 tensor of at least (dots_cap, 3)")
+        dbuf = dots_buf.numpy().view(np.uint32)
+    else:
+        dbuf = np.empty((max(cap, 1), 3), dtype=np.uint32)   # the library fills the first count rows
     cnt = ctypes.c_int64()
     ld = out.stride(0) if rows > 1 else max(cols, out.shape[1])
     st = lib.ap_alignment_plot_host(ctypes.c_void_p(xt.data_ptr()), m, ctypes.c_void_p(yt.data_ptr()), n, w,
@@ -314,6 +323,16 @@ def alignment_plot_host(x, y, w: int, scores=LCS, out=None, threshold=None,
     d = dbuf[:k].astype(np.int64)
     d[:, 2] &= 0xFFFF          # value, without the pad half-word
     return out, d, cnt.value
+
+
+def plot_host_workspace_size(m: int, n: int, w: int, scores=LCS, out_elem_bytes: int = 1,
+                             dots_cap: int = 0) -> int:
+    """Bytes of device workspace alignment_plot_host needs."""
+    need = ctypes.c_int64()
+    sc = _scores(scores)
+    _check(load().ap_plot_host_workspace_size(m, n, w, ctypes.byref(sc), int(out_elem_bytes),
+                                              int(dots_cap), ctypes.byref(need)))
+    return need.value
 
 
 def _dots_tensor(count: int, device):

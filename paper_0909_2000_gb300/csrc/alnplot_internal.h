@@ -4,10 +4,21 @@
 #include <cstdint>
 #include <string>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/alnplot.h"
 
 namespace ap {
+
+// Scoped NVTX range around a host-side phase of a call (comb launches, dot
+// passes, band copies, batch and server work), for timeline profilers; a
+// no-op unless a profiling tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Records a message for ap_last_error() on the calling thread and returns s.
 ap_status fail(ap_status s, const char *fmt, ...);

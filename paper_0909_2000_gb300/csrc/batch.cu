@@ -500,6 +500,7 @@ ap_status ap_batch_run(ap_batch *b, void *stream)
 {
     if (!b) return fail(AP_E_INVAL, "ap_batch_run: null batch");
     if (!b->exec) return AP_OK;
+    NvtxRange range("alnplot: batch graph launch");
     cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e, "ap_batch_run");
     return AP_OK;

@@ -257,6 +257,7 @@ cudaError_t dots_pass(const void *plot, int elem_bytes, int64_t rows, int64_t co
                       int64_t *offsets, int64_t *running, cudaStream_t stream)
 {
     if (rows <= 0) return cudaSuccess;
+    NvtxRange range("alnplot: dots pass");
     const int threads = 256, rows_per_block = threads / 32;
     const int grid = grid_for(rows, rows_per_block);
     const int vec = ((uintptr_t)plot % 16 == 0) && ((ld * elem_bytes) % 16 == 0);
@@ -280,6 +281,7 @@ cudaError_t dots_pass(const void *plot, int elem_bytes, int64_t rows, int64_t co
 cudaError_t checksum_pass(const void *plot, int elem_bytes, int64_t rows, int64_t cols,
                           int64_t ld, int nbins, uint64_t *result, cudaStream_t stream)
 {
+    NvtxRange range("alnplot: checksum");
     cudaError_t e = cudaMemsetAsync(result, 0, sizeof(uint64_t) * (size_t)(1 + nbins), stream);
     if (e != cudaSuccess || rows <= 0 || cols <= 0) return e;
     const int grid = grid_for(rows, 1) > 4096 ? 4096 : grid_for(rows, 1);

@@ -14,6 +14,7 @@
 //   comb, and the band copy waits behind them).
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "alnplot_internal.h"
 #include "plan.h"
@@ -24,6 +25,45 @@ namespace {
 constexpr int64_t kHostBand = 1LL << 30;     // bytes per device band buffer (several waves of tiles)
 
 int64_t align256(int64_t v) { return (v + 255) & ~(int64_t)255; }
+
+// The copy stream and band events of ap_alignment_plot_host, created once per
+// calling thread and device and reused by every later call (they live until
+// the process exits).
+struct HostPlotStreams {
+    int device = -1;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t combed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+};
+
+cudaError_t host_plot_streams(HostPlotStreams **out)
+{
+    static thread_local std::vector<HostPlotStreams> cache;
+    const int dev = current_device();
+    for (auto &r : cache)
+        if (r.device == dev) {
+            *out = &r;
+            return cudaSuccess;
+        }
+    HostPlotStreams r;
+    r.device = dev;
+    cudaError_t e = cudaStreamCreateWithFlags(&r.copy, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&r.combed[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.copied[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        if (r.copy) cudaStreamDestroy(r.copy);
+        for (int k = 0; k < 2; ++k) {
+            if (r.combed[k]) cudaEventDestroy(r.combed[k]);
+            if (r.copied[k]) cudaEventDestroy(r.copied[k]);
+        }
+        return e;
+    }
+    cache.reserve(8);
+    cache.push_back(r);
+    *out = &cache.back();
+    return cudaSuccess;
+}
 
 struct HostLayout {
     int64_t band_rows = 0, band_ld = 0, x_off = 0, y_off = 0, buf_off[2] = {0, 0},
@@ -99,6 +139,7 @@ ap_status ap_alignment_plot_host(const uint8_t *x, int64_t m, const uint8_t *y, 
         return fail(AP_E_NOMEM, "workspace of %lld bytes given, %lld needed",
                     (long long)workspace_bytes, (long long)L.total);
     const bool want_dots = dots_count != nullptr;
+    NvtxRange range("alnplot: plot into host memory");
     char *ws = (char *)workspace;
     uint8_t *dx = (uint8_t *)(ws + L.x_off), *dy = (uint8_t *)(ws + L.y_off);
     int64_t *running = (int64_t *)(ws + L.running_off);
@@ -106,13 +147,14 @@ ap_status ap_alignment_plot_host(const uint8_t *x, int64_t m, const uint8_t *y, 
     cudaStream_t st = (cudaStream_t)stream;
 
     // the caller's stream combs every band; the copy stream moves them out
-    cudaStream_t cs[2] = {st, st}, copy = nullptr;
-    cudaEvent_t combed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
-    cudaError_t e = cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        e = cudaEventCreateWithFlags(&combed[k], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[k], cudaEventDisableTiming);
-    }
+    cudaStream_t cs[2] = {st, st};
+    HostPlotStreams *hs = nullptr;
+    cudaError_t e = host_plot_streams(&hs);
+    if (e != cudaSuccess) return fail_cuda(e, "ap_alignment_plot_host: copy stream");
+    cudaStream_t copy = hs->copy;
+    cudaEvent_t *combed = hs->combed, *copied = hs->copied;
+    // the previous call on this thread has finished with the copy stream
+    // (every call synchronises it before returning)
     if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, (size_t)m, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, (size_t)n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && want_dots) e = cudaMemsetAsync(running, 0, sizeof(int64_t), st);
@@ -167,12 +209,10 @@ ap_status ap_alignment_plot_host(const uint8_t *x, int64_t m, const uint8_t *y, 
         if (e == cudaSuccess && keep > 0)
             e = cudaMemcpy(dots, ddots, (size_t)keep * sizeof(ap_dot), cudaMemcpyDeviceToHost);
     }
-    for (int k = 0; k < 2; ++k) {
-        if (combed[k]) cudaEventDestroy(combed[k]);
-        if (copied[k]) cudaEventDestroy(copied[k]);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(copy);      // leave the reused copy stream idle
+        return fail_cuda(e, "ap_alignment_plot_host");
     }
-    if (copy) cudaStreamDestroy(copy);
-    if (e != cudaSuccess) return fail_cuda(e, "ap_alignment_plot_host");
     if (want_dots) {
         *dots_count = total;
         if (total > dots_cap)

@@ -5,6 +5,7 @@
 #include <utility>
 #include <vector>
 
+#include "alnplot_internal.h"
 #include "plan.h"
 
 namespace ap {
@@ -309,6 +310,7 @@ cudaError_t launch_comb(const Plan &pl, const uint8_t *x, int64_t m, const uint8
                         int64_t n, void *out, int out_bytes, int64_t ld, cudaStream_t stream)
 {
     if (pl.ntiles == 0) return cudaSuccess;
+    NvtxRange range("alnplot: comb launch");
     cudaError_t e0 = raise_smem_limit((const void *)pl.v->fn);
     if (e0 != cudaSuccess) return e0;
     CombParams p;

@@ -174,6 +174,7 @@ cudaError_t grow_pinned(void **p, int64_t *cap, int64_t need)
 // Enqueue a job's whole GPU work on its slot's stream (phase 1).
 cudaError_t start_job(ap_server *s, Slot &slot, Job &j)
 {
+    NvtxRange range("alnplot: server job start");
     cudaStream_t st = slot.stream;
     const int64_t m = (int64_t)j.x.size(), n = (int64_t)j.y.size();
     cudaError_t e = grow_pinned((void **)&slot.pin_in, &slot.pin_in_cap, m + n);
