@@ -186,9 +186,10 @@ ap_status ap_alignment_plot(const uint8_t *x, int64_t m, const uint8_t *y,
  * row r holds the x-window starting at
  * r * step, for 0 <= r < ceil((m - w) / step), against every y-window:
  *     out[r*ld + j] = P[r * step][j]
- * step = 1 is ap_alignment_plot.  With step > 1 this build covers LCS and
- * {2,1,0} for w <= 120 (AP_E_UNSUPPORTED otherwise).  Other arguments and
- * errors as in ap_alignment_plot; AP_E_INVAL for step < 1.
+ * step = 1 is ap_alignment_plot.  With step > 1 this build covers LCS for
+ * w <= 512 and {2,1,0} for w <= 256 (AP_E_UNSUPPORTED otherwise, and for
+ * other score schemes).  Other arguments and errors as in
+ * ap_alignment_plot; AP_E_INVAL for step < 1.
  */
 ap_status ap_alignment_plot_step(const uint8_t *x, int64_t m, const uint8_t *y,
                                  int64_t n, int32_t w, const ap_scores *scores,
@@ -313,6 +314,19 @@ ap_status ap_plot_dots_noalloc(const void *plot, int32_t elem_bytes,
 ap_status ap_plot_checksum(const void *plot, int32_t elem_bytes, int64_t rows,
                            int64_t cols, int64_t ld, int32_t nbins,
                            uint64_t *result, void *stream);
+
+/*
+ * Debug builds only (the library compiled with AP_DEBUG_BOUNDS, as
+ * paper_0909_2000_gb300/build.py builds libalnplot_debug.so): every plot
+ * store, sequence read, exit-ring slot and match-table read of the comb
+ * kernels is checked against its buffer, and a failed check sets a bit in a
+ * per-device word and skips the access instead of touching memory outside
+ * the buffer.  This call waits for the device, writes that word to *flags
+ * (host; 0 = no violation; bits 1 plot store, 2 y read, 4 x read, 8 ring
+ * slot, 16 table read) and clears it.  Other builds return
+ * AP_E_UNSUPPORTED with *flags = 0.  Not in the paper: a testing aid.
+ */
+ap_status ap_debug_bounds(uint32_t *flags);
 
 /* ------------------------------------------------------------------------
  * Batched plots: many independent (x, y, w) jobs, run as one CUDA graph of

@@ -111,6 +111,7 @@ def _declare(lib):
         "ap_plot_dots": [p, i32, i64, i64, i64, i32, p, i64, i64p, p, i64, p],
         "ap_plot_checksum": [p, i32, i64, i64, i64, i32, u64p, p],
         "ap_plot_dots_noalloc": [p, i32, i64, i64, i64, i32, p, i64, i64p, p],
+        "ap_debug_bounds": [ctypes.POINTER(ctypes.c_uint32)],
         "ap_batch_create": [ctypes.POINTER(ap_job), i32, ctypes.POINTER(ap_batch_options),
                             ctypes.POINTER(ctypes.c_void_p)],
         "ap_batch_run": [p, p],
@@ -133,7 +134,9 @@ def _declare(lib):
 
 
 def library_path() -> str:
-    return os.path.join(_HERE, "libalnplot.so")
+    """The library to load: $AP_LIB if set (e.g. the bounds-checked debug
+    build), else the in-tree libalnplot.so."""
+    return os.environ.get("AP_LIB") or os.path.join(_HERE, "libalnplot.so")
 
 
 def load(build_if_missing: bool = True):
@@ -142,7 +145,7 @@ def load(build_if_missing: bool = True):
     with _lock:
         if _lib is None:
             path = library_path()
-            if build_if_missing:
+            if build_if_missing and not os.environ.get("AP_LIB"):
                 from . import build as _build
                 path = _build.build()
             if not os.path.exists(path):
@@ -458,6 +461,14 @@ def plot_dots_noalloc(plot, threshold: int, dots, cap: int | None = None, stream
         err.count = cnt.value
         raise err
     return dots, cnt.value
+
+
+def debug_bounds() -> int:
+    """Bounds-check violation bits since the last call (debug builds only;
+    raises ApError(AP_E_UNSUPPORTED) in other builds)."""
+    f = ctypes.c_uint32()
+    _check(load().ap_debug_bounds(ctypes.byref(f)))
+    return f.value
 
 
 def plot_checksum(plot, nbins: int, stream=None):

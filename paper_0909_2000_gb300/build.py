@@ -70,24 +70,53 @@ def _variants():
             v.append(("U16Lanes", 15, 16, nu * rp, 8, nu, mu, 4))
     v = [t + (False,) for t in v]
     # vertical step h > 1 (one x word per unit): LCS w <= 120 and {2,1,0} w <= 120
+    # in 8-bit lanes with 7-bit keys
     for r in range(8, 65, 8):
         v.append(("U8Lanes", 7, 8, r, 1, 1, 0, 8, True))
     for r in range(36, 61, 4):
         v.append(("U8Lanes", 7, 8, r, 2, 1, 0, 8, True))
     for rp in range(2, 33, 2):
         v.append(("U8Lanes", 7, 8, 2 * rp, 4, 2, 1, min(4, rp), True))
+    # ... LCS 120 < w <= 254 in full 8-bit keys, LCS w <= 512 and {2,1,0}
+    # w <= 256 in 16-bit lanes
+    v.append(("U8FLanes", 8, 8, 64, 2, 1, 0, 8, True))
+    for r in range(32, 65, 4):
+        v.append(("U8FLanes", 8, 8, r, 4, 1, 0, 8, True))
+    for g in (4, 8):
+        for r in range(16, 65, 8):
+            v.append(("U16Lanes", 15, 16, r, g, 1, 0, 8, True))
+    for rp in range(16, 33, 4):
+        v.append(("U16Lanes", 15, 16, 2 * rp, 8, 2, 1, 4, True))
     return v
 
 
 VARIANTS = _variants()
 NUNITS = 12   # translation units for the instantiations
 
+# The bounds-checked debug build (AP_DEBUG_BOUNDS) compiles a few variants
+# only, one of each kind of kernel the tests exercise: LCS in 7-bit keys on
+# one thread (w 13..16 and 97..100) and two threads, full 8-bit keys on two
+# threads, 16-bit lanes on four, 10-bit lanes on four; {2,1,0} on one thread
+# and in 16-bit lanes; {3,1,0}; the vertical-step layout.
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(HERE, "libalnplot_debug.so")
+DEBUG_KINDS = {("U8Lanes", 16, 1, 1, 0, False), ("U8Lanes", 100, 1, 1, 0, False),
+               ("U8Lanes", 40, 2, 1, 0, False), ("U8FLanes", 64, 2, 1, 0, False),
+               ("U16Lanes", 64, 4, 1, 0, False), ("U10Lanes", 75, 4, 1, 0, False),
+               ("U8Lanes", 48, 1, 2, 1, False), ("U16Lanes", 64, 8, 2, 1, False),
+               ("U8Lanes", 24, 1, 3, 1, False), ("U8Lanes", 16, 1, 1, 0, True)}
 
-def _generate() -> list[str]:
-    gen = os.path.join(BUILD, "gen")
+
+def _debug_variants():
+    return [v for v in VARIANTS if (v[0], v[3], v[4], v[5], v[6], v[8]) in DEBUG_KINDS]
+
+
+def _generate(build_dir: str = BUILD, variants=None) -> list[str]:
+    variants = VARIANTS if variants is None else variants
+    gen = os.path.join(build_dir, "gen")
     os.makedirs(gen, exist_ok=True)
     paths = []
-    parts = [VARIANTS[k::NUNITS] for k in range(NUNITS)]
+    parts = [variants[k::NUNITS] for k in range(NUNITS)]
     for k, part in enumerate(parts):
         lines = ['#include "variants.h"', "namespace ap {",
                  "extern const Variant kVariants%d[];" % k,
@@ -122,15 +151,16 @@ def _write_if_changed(path: str, text: str) -> str:
     return path
 
 
-def _flags():
+def _flags(debug: bool = False):
     # AP_KERNEL_DIGEST keys the batch autotuner's persistent cache to these
     # comb kernels
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                    "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE,
-                   "-DAP_KERNEL_DIGEST=\"comb-%s\"" % kernel_digest()]
+                   "-DAP_KERNEL_DIGEST=\"comb-%s%s\"" % (kernel_digest(), "-debug" if debug else "")] + \
+        (["-DAP_DEBUG_BOUNDS"] if debug else [])
 
 
-def _deps_digest() -> str:
+def _deps_digest(debug: bool = False) -> str:
     h = hashlib.sha1()
     for d in (CSRC, INCLUDE):
         for name in sorted(os.listdir(d)):
@@ -138,8 +168,8 @@ def _deps_digest() -> str:
             if os.path.isfile(p):
                 h.update(name.encode())
                 h.update(open(p, "rb").read())
-    h.update(repr(VARIANTS).encode())
-    h.update(repr(_flags()).encode())
+    h.update(repr(_debug_variants() if debug else VARIANTS).encode())
+    h.update(repr(_flags(debug)).encode())
     return h.hexdigest()
 
 
@@ -161,8 +191,8 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def _compile(src: str, obj: str, verbose: bool) -> None:
-    cmd = [NVCC] + _flags() + ["-c", src, "-o", obj]
+def _compile(src: str, obj: str, verbose: bool, debug: bool = False) -> None:
+    cmd = [NVCC] + _flags(debug) + ["-c", src, "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -170,34 +200,38 @@ def _compile(src: str, obj: str, verbose: bool) -> None:
         raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, r.stdout, r.stderr))
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    """Compile (if sources changed) and return the path of libalnplot.so."""
-    os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, "stamp")
-    digest = _deps_digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == digest:
-        return LIB
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
+          debug: bool = False) -> str:
+    """Compile (if sources changed) and return the path of libalnplot.so, or
+    with debug=True of libalnplot_debug.so (bounds checks, a few variants)."""
+    bdir, lib = (DEBUG_BUILD, DEBUG_LIB) if debug else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
+    stamp = os.path.join(bdir, "stamp")
+    digest = _deps_digest(debug)
+    if not force and os.path.exists(lib) and os.path.exists(stamp) and open(stamp).read() == digest:
+        return lib
     if shutil.which(NVCC) is None and not os.path.exists(NVCC):
         raise RuntimeError("nvcc not found; the CUDA library cannot be built")
     srcs = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cu")]
-    srcs += _generate()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    srcs += _generate(bdir, _debug_variants() if debug else None)
+    objs = [os.path.join(bdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
     jobs = jobs or min(len(srcs), max(1, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(jobs) as ex:
-        list(ex.map(lambda so: _compile(so[0], so[1], verbose), zip(srcs, objs)))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+        list(ex.map(lambda so: _compile(so[0], so[1], verbose, debug), zip(srcs, objs)))
+    LIB_ = lib
+    tmp = LIB_ + ".%d.tmp" % os.getpid()
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, LIB_)
     with open(stamp, "w") as f:
         f.write(digest)
-    return LIB
+    return LIB_
 
 
 if __name__ == "__main__":
     import time
     t = time.time()
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))
     print("built in %.1f s" % (time.time() - t))

@@ -360,6 +360,23 @@ ap_status ap_plot_dots(const void *plot, int32_t elem_bytes, int64_t rows, int64
     return AP_OK;
 }
 
+ap_status ap_debug_bounds(uint32_t *flags)
+{
+    if (!flags) return fail(AP_E_INVAL, "ap_debug_bounds: null pointer");
+    *flags = 0;
+#ifdef AP_DEBUG_BOUNDS
+    uint32_t *d = debug_flags();
+    if (!d) return fail(AP_E_CUDA, "ap_debug_bounds: no violation word on this device");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(flags, d, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) return fail_cuda(e, "ap_debug_bounds");
+    return AP_OK;
+#else
+    return fail(AP_E_UNSUPPORTED, "this build has no bounds checks (built without AP_DEBUG_BOUNDS)");
+#endif
+}
+
 ap_status ap_plot_checksum(const void *plot, int32_t elem_bytes, int64_t rows, int64_t cols,
                            int64_t ld, int32_t nbins, uint64_t *result, void *stream)
 {

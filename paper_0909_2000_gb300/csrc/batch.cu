@@ -112,7 +112,10 @@ void store_tune_cache(const std::string &key, const Schedule &sc)
     fclose(f);
 }
 
-std::string tune_key(int device, int nu, int mu, int w)
+// The key also holds the class's size, as log2 buckets of its job count and
+// its cells: the best schedule of a few small plots is not that of a
+// thousand large ones.
+std::string tune_key(int device, int nu, int mu, int w, int64_t njobs, double cells)
 {
     cudaDeviceProp prop;
     std::string name = "unknown";
@@ -125,9 +128,15 @@ std::string tune_key(int device, int nu, int mu, int w)
     }
     for (char &c : name)
         if (c == ' ' || c == '|') c = '_';
+    int jb = 0, cb = 0;
+    while ((1LL << (jb + 1)) <= njobs) ++jb;
+    while (cells >= 2.0 && cb < 80) {
+        cells /= 2.0;
+        ++cb;
+    }
     char buf[400];
-    snprintf(buf, sizeof buf, "%s %s sms=%d nu=%d mu=%d w=%d ", AP_KERNEL_DIGEST, name.c_str(), sms,
-             nu, mu, w);
+    snprintf(buf, sizeof buf, "%s %s sms=%d nu=%d mu=%d w=%d jobs=2^%d cells=2^%d ", AP_KERNEL_DIGEST,
+             name.c_str(), sms, nu, mu, w, jb, cb);
     return buf;
 }
 
@@ -407,7 +416,9 @@ ap_status ap_batch_create(const ap_job *jobs, int32_t njobs, const ap_batch_opti
             classes[std::make_tuple(b->plans[j].nu, b->plans[j].mu, b->plans[j].w)].push_back((int)j);
         for (auto &kv : classes) {
             const int nu = std::get<0>(kv.first), mu = std::get<1>(kv.first), w = std::get<2>(kv.first);
-            const std::string key = tune_key(b->device, nu, mu, w);
+            double cells = 0.0;
+            for (int j : kv.second) cells += (double)b->plans[j].rows * b->plans[j].cols * w;
+            const std::string key = tune_key(b->device, nu, mu, w, (int64_t)kv.second.size(), cells);
             Schedule best;
             bool cached = false;
             {

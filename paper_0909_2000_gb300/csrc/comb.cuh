@@ -96,7 +96,30 @@ struct CombParams {
     int32_t warp_words; // shared-memory words per warp of a plain launch
     uint32_t scale;     // plot values are scale x the comb's values (gcd of the scores)
     int32_t tab;        // 1: the aligned row split of the G > 1 table path fits (tabg_split_ok)
+    uint32_t *dbg;      // debug builds: violation bits of the bounds checks (device), else null
 };
+
+// Bounds checks of debug builds (compiled with AP_DEBUG_BOUNDS): a failed
+// check sets its bit in *p.dbg and the access it guards is skipped, so a
+// wrong index is reported (ap_debug_bounds) instead of touching memory
+// outside its buffer.  In other builds every check is the constant true.
+enum : uint32_t {
+    kDbgPlotStore = 1u,    // a plot store outside rows x cols
+    kDbgYRead = 2u,        // a y read outside [0, n)
+    kDbgXRead = 4u,        // an x read outside [0, m)
+    kDbgRing = 8u,         // an exit-ring slot outside the ring
+    kDbgTable = 16u,       // a match-table read outside the tables
+};
+#ifdef AP_DEBUG_BOUNDS
+__device__ __forceinline__ bool ap_check(uint32_t *flag, bool ok, uint32_t code)
+{
+    if (!ok && flag) atomicOr(flag, code);
+    return ok;
+}
+#define AP_CHECK(p, cond, code) ap_check((p).dbg, (cond), (code))
+#else
+#define AP_CHECK(p, cond, code) true
+#endif
 
 // ---------------------------------------------------------------------------
 // SWAR lane formats
@@ -360,7 +383,7 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
             uint32_t o4[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) o4[k] = prmt(prmt(wv[2 * k], wv[2 * k + 1], sel), 0u, 0x4140u) * sc;
-            if (i < p.rows)
+            if (i < p.rows && AP_CHECK(p, jbase + 8 * part + 8 <= p.cols, kDbgPlotStore))
                 *(uint4 *)((uint16_t *)p.out + i * p.ld + jbase + 8 * part) =
                     make_uint4(o4[0], o4[1], o4[2], o4[3]);
         }
@@ -386,7 +409,7 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
             for (int k = 0; k < 4; ++k)
                 o4[k] = prmt(prmt(wv[4 * k], wv[4 * k + 1], sel), prmt(wv[4 * k + 2], wv[4 * k + 3], sel),
                              0x5410u) * sc;
-            if (i < p.rows)
+            if (i < p.rows && AP_CHECK(p, jbase + 16 * half + 16 <= p.cols, kDbgPlotStore))
                 *(uint4 *)((uint8_t *)p.out + i * p.ld + jbase + 16 * half) =
                     make_uint4(o4[0], o4[1], o4[2], o4[3]);
         }
@@ -400,6 +423,7 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
             const int rw = it * 4 + (lane >> 3);
             const int64_t i = iw + rw;
             if (i >= p.rows || j4 >= cnt) continue;
+            if (!AP_CHECK(p, jbase + (j4 + 4 <= cnt ? j4 + 4 : cnt) <= p.cols, kDbgPlotStore)) continue;
             const int grp = rw / NS, b = rw % NS;
             const uint32_t *sp = stage + j4 * (NGRP + 1) + grp;
             const uint32_t w0 = sp[0], w1 = sp[NGRP + 1], w2 = sp[2 * (NGRP + 1)], w3 = sp[3 * (NGRP + 1)];
@@ -463,7 +487,7 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
         for (int rw = 0; rw < SPW; ++rw) {
             const int64_t i = iw + rw;
             if (i >= p.rows) break;
-            if (lane < cnt) {
+            if (lane < cnt && AP_CHECK(p, jbase + lane < p.cols, kDbgPlotStore)) {
                 const uint32_t v = lane_of<L>(stage[lane * (NGRP + 1) + rw / NS], rw % NS) * sc;
                 const int64_t off = i * p.ld + jbase + lane;
                 if (p.out_bytes == 1) ((uint8_t *)p.out)[off] = (uint8_t)v;
@@ -539,7 +563,7 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
 #pragma unroll
             for (int t = 0; t < L::RPW; ++t) {
                 const int64_t idx = base + q * L::RPW + t;
-                const uint32_t c = (idx < p.m) ? (uint32_t)__ldg(p.x + idx) : 0u;
+                const uint32_t c = (idx < p.m && AP_CHECK(p, idx >= 0, kDbgXRead)) ? (uint32_t)__ldg(p.x + idx) : 0u;
                 wv |= c << (L::BITS * t);
             }
             xw[q] = wv;
@@ -551,7 +575,7 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
 #pragma unroll
             for (int b = 0; b < NS; ++b) {
                 const int64_t idx = (ig + b) * p.step + ub + q;
-                const uint32_t c = (idx < p.m) ? (uint32_t)__ldg(p.x + idx) : 0u;
+                const uint32_t c = (idx < p.m && AP_CHECK(p, idx >= 0, kDbgXRead)) ? (uint32_t)__ldg(p.x + idx) : 0u;
                 wv |= c << (L::BITS * b);
             }
             xw[q] = wv;
@@ -639,6 +663,7 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
             for (int b = 0; b < NS; ++b) {
                 const uint32_t slot = SCORE ? (slots >> (8 * b)) & (uint32_t)ring_mask
                                             : prmt(slots, 0u, 0x4440u | (uint32_t)b);
+                if (!AP_CHECK(p, slot < (uint32_t)p.ring, kDbgRing)) continue;
                 uint8_t *e = ring8 + slot * (uint32_t)(NGRP * 4) + b;
                 const uint8_t f = SCORE ? (uint8_t)((valid >> (8 * b)) & 1u)
                                         : (uint8_t)prmt(valid, 0u, 0x4440u | (uint32_t)b);
@@ -690,6 +715,7 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
     // step, is at most n - 1).  Skewed threads clamp.
     auto ychar = [&](int yi) -> uint32_t {
         if (G > 1) yi = yi < 0 ? 0 : (yi > ylast ? ylast : yi);
+        if (!AP_CHECK(p, yi >= 0 && yi <= ylast, kDbgYRead)) return 0u;
         return (uint32_t)__ldg(ytile + yi);
     };
 
@@ -912,7 +938,10 @@ __host__ __device__ constexpr bool has_tables(int key_bits, int groups, int nu, 
 #define AP_TAB_CPS 2   // plot columns per step of the table path (2 or 4)
 #endif
 #ifndef AP_TAB_HNF
-#define AP_TAB_HNF 0   // columns of each step whose right output is formed on the FMA pipe
+// Columns of each step whose right output is formed on the FMA pipe: one of
+// the two measured 62.2 ms against 65.3 ms for none and 65.9 ms for both
+// (100k DNA, w = 100, comb alone).
+#define AP_TAB_HNF 1
 #endif
 
 // Builds the warp's tables; false (warp-uniform) if the x characters of the
@@ -1071,6 +1100,9 @@ __device__ __forceinline__ void comb_tile_tab(const CombParams &p, int64_t sg, i
     const uint32_t one = p.one;
     const uint32_t neg1 = 0u - p.one;
     const uint32_t tgrp = smem_addr(tab + 4 * grp);   // this thread's row words start here
+    const uint32_t tlo = smem_addr(tab), thi = tlo + 4u * (uint32_t)((kTabSyms + 1) * P);
+    (void)tlo;
+    (void)thi;
 
     int kc = wk;
     int since = 0;
@@ -1086,6 +1118,7 @@ __device__ __forceinline__ void comb_tile_tab(const CombParams &p, int64_t sg, i
 #pragma unroll
         for (int b = 0; b < NS; ++b) {
             const uint32_t slot = prmt(slots, 0u, 0x4440u | (uint32_t)b);
+            if (!AP_CHECK(p, slot < (uint32_t)p.ring, kDbgRing)) continue;
             ring8[slot * (uint32_t)(NGRP * 4) + b] = (uint8_t)prmt(valid, 0u, 0x4440u | (uint32_t)b);
         }
     };
@@ -1096,6 +1129,7 @@ __device__ __forceinline__ void comb_tile_tab(const CombParams &p, int64_t sg, i
     };
     auto ychar = [&](int yi) -> uint32_t {
         yi = yi > ylast ? ylast : yi;
+        if (!AP_CHECK(p, yi >= 0, kDbgYRead)) return 0u;
         return (uint32_t)__ldg(ytile + yi);
     };
 
@@ -1130,7 +1164,10 @@ __device__ __forceinline__ void comb_tile_tab(const CombParams &p, int64_t sg, i
         for (int j = 0; j < R / 4; ++j) {
             uint4 X[CPS];
 #pragma unroll
-            for (int c = 0; c < CPS; ++c) X[c] = lds128(tcol[c] + 16u * (uint32_t)j);
+            for (int c = 0; c < CPS; ++c) {
+                const uint32_t a = tcol[c] + 16u * (uint32_t)j;
+                X[c] = AP_CHECK(p, a >= tlo && a + 16u <= thi, kDbgTable) ? lds128(a) : make_uint4(0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u);
+            }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int k = 4 * j + r;
@@ -1397,6 +1434,9 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
     const uint32_t neg1 = 0u - p.one;
     const uint32_t sph = p.spread_hi, spl = p.spread_lo;
     const uint32_t tbase = smem_addr(tab + g * S + NS * grp);   // this thread's row 0, symbol 0
+    const uint32_t tlo = smem_addr(tab + g * S), thi = tlo + 4u * (uint32_t)((kTabSyms + 1) * Q);
+    (void)tlo;
+    (void)thi;
 
     int kc = wk;
     int since = 0;
@@ -1415,6 +1455,7 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
 #pragma unroll
             for (int b = 0; b < NS; ++b) {
                 const uint32_t slot = prmt(slots, 0u, 0x4440u | (uint32_t)b);
+                if (!AP_CHECK(p, slot < (uint32_t)p.ring, kDbgRing)) continue;
                 ring8[slot * (uint32_t)(NGRP * 4) + b] = (uint8_t)prmt(valid, 0u, 0x4440u | (uint32_t)b);
             }
         } else {
@@ -1449,6 +1490,7 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
     };
     auto ychar = [&](int yi) -> uint32_t {
         yi = yi < 0 ? 0 : (yi > ylast ? ylast : yi);
+        if (!AP_CHECK(p, yi >= 0 && yi <= ylast, kDbgYRead)) return 0u;
         return (uint32_t)__ldg(ytile + yi);
     };
 
@@ -1474,8 +1516,11 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
 #pragma unroll
         for (int j = 0; j < R / RPL; ++j) {
             uint32_t X0[RPL], X1[RPL];
-            lds_rows<RPL>(t0 + 4u * (uint32_t)(RPL * j), X0);
-            lds_rows<RPL>(t1 + 4u * (uint32_t)(RPL * j), X1);
+            const uint32_t a0 = t0 + 4u * (uint32_t)(RPL * j), a1 = t1 + 4u * (uint32_t)(RPL * j);
+            if (AP_CHECK(p, a0 >= tlo && a0 + 4u * RPL <= thi, kDbgTable)) lds_rows<RPL>(a0, X0);
+            else for (int r = 0; r < RPL; ++r) X0[r] = nomatch;
+            if (AP_CHECK(p, a1 >= tlo && a1 + 4u * RPL <= thi, kDbgTable)) lds_rows<RPL>(a1, X1);
+            else for (int r = 0; r < RPL; ++r) X1[r] = nomatch;
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
                 const int k = RPL * j + r;

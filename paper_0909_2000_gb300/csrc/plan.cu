@@ -53,12 +53,27 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
         return true;
     };
     if (xrows) {
-        // Vertical step: one x word per unit; LCS and {2,1,0} up to w = 120.
-        kbits = 7;
+        // Vertical step: one x word per unit.  LCS: 7-bit keys up to w = 120,
+        // full 8-bit keys up to 254, 16-bit lanes up to 512; {2,1,0}: 7-bit
+        // pair keys up to 120, 16-bit lanes up to 256.
         if (!score && w <= 120) {
+            kbits = 7;
             if (!rows_for(1, 8, 8, 64)) rows_for(2, 4, 36, 60);
+        } else if (!score && w <= 254) {
+            kbits = 8;
+            if (want_groups == 4 || !rows_for(2, 64, 64, 64)) rows_for(4, 4, 32, 64);
+        } else if (!score) {
+            kbits = 15;
+            if (want_groups != 8 && rows_for(4, 8, 16, 64)) {
+            } else {
+                rows_for(8, 8, 16, 64);
+            }
         } else if (nu == 2 && mu == 1 && w <= 120) {
+            kbits = 7;
             if (rows_for(4, 2, 2, 32)) rows *= 2;
+        } else if (nu == 2 && mu == 1) {
+            kbits = 15;
+            if (rows_for(8, 4, 16, 32)) rows *= 2;
         }
     } else if (!score) {
         // A lane-format request (8, 10 or 16 bits) is honoured where that
@@ -244,6 +259,28 @@ int64_t physical_cells(const Plan &pl)
     return pl.nsg * (int64_t)pl.strips_per_warp * cols_phys * comb_rows_padded;
 }
 
+#ifdef AP_DEBUG_BOUNDS
+uint32_t *debug_flags()
+{
+    static std::mutex mu;
+    static std::vector<std::pair<int, uint32_t *>> flags;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &f : flags)
+        if (f.first == dev) return f.second;
+    uint32_t *d = nullptr;
+    if (cudaMalloc(&d, sizeof(uint32_t)) != cudaSuccess || cudaMemset(d, 0, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    flags.emplace_back(dev, d);
+    return d;
+}
+#else
+uint32_t *debug_flags() { return nullptr; }
+#endif
+
 void fill_params(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y, int64_t n,
                  void *out, int out_bytes, int64_t ld, CombParams *p)
 {
@@ -289,6 +326,7 @@ void fill_params(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y, 
     const Variant *v = pl.v;
     p->tab = has_tables_g(v->key_bits, v->groups, v->nu, v->xrows != 0) &&
              tabg_split_ok(pl.w, v->groups, v->rows, tabg_rpl(v->lane_bits == 8 ? 4 : 2), v->padu);
+    p->dbg = debug_flags();
 }
 
 cudaError_t raise_smem_limit(const void *fn)

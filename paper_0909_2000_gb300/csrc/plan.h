@@ -41,6 +41,10 @@ void tile_plan(Plan *pl, int64_t rows, int64_t cols, int64_t chunk_hint, int dev
 void fill_params(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y, int64_t n,
                  void *out, int out_bytes, int64_t ld, CombParams *p);
 
+// Debug builds (AP_DEBUG_BOUNDS): the current device's word of bounds-check
+// violation bits (allocated on first use); null in other builds.
+uint32_t *debug_flags();
+
 // Raises a kernel's dynamic shared-memory limit (once per kernel and device).
 cudaError_t raise_smem_limit(const void *fn);
 

@@ -2,9 +2,10 @@
 // continuous batching across concurrent jobs.
 //
 // Requests (host sequences, window, threshold) are copied in and queued.  A
-// scheduler thread admits them in arrival order while a slot is free and the
-// job's device memory fits the budget.  An admitted job runs on its slot's
-// own stream:
+// scheduler thread admits them in arrival order, every job that fits a free
+// slot and the device-memory budget (a job that does not fit yet does not
+// block the ones behind it; one that has waited two seconds gets the next
+// room).  An admitted job runs on its slot's own stream:
 //   * copy x, y in and reset the running dot count;
 //   * comb the plot band by band into the job's band buffer, each band
 //     followed by its dot extraction (count, scan, write, appended in
@@ -210,90 +211,126 @@ cudaError_t start_job(ap_server *s, Slot &slot, Job &j)
     return e;
 }
 
+// Admission policy: queued jobs are taken in arrival order, and every job
+// that fits (a free slot, and its device memory within the budget) is
+// admitted, so a large job at the head does not hold back the small ones
+// behind it.  To keep large jobs from starving, once the oldest queued job
+// has waited kAgeLimit it is admitted first: younger jobs are then only
+// admitted while they leave room for it.
+constexpr auto kAgeLimit = std::chrono::milliseconds(2000);
+
 void scheduler(ap_server *s)
 {
     cudaSetDevice(s->device);
+    struct Start {
+        Slot *slot;
+        Job *job;
+        cudaError_t err;
+    };
+    struct Done {
+        Slot *slot;
+        Job *job;
+        int phase;          // the phase that finished: 1 comb and dots, 2 result copy
+        cudaError_t err;
+    };
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
         bool busy = false;
         for (auto &sl : s->slots) busy |= sl.job != nullptr;
         if (s->stop && !busy) break;
-        // Admit queued jobs in arrival order while a slot and memory are free.
-        while (!s->stop && !s->queue.empty()) {
-            Job *j = s->queue.front();
-            if (j->cancelled) {
-                s->queue.pop_front();
-                finish(s, nullptr, j, AP_E_CANCELLED);
-                continue;
-            }
-            if (j->plan.rows == 0 || j->plan.cols == 0) {   // empty plot: nothing to run
-                s->queue.pop_front();
-                j->count = 0;
-                finish(s, nullptr, j, AP_OK);
-                continue;
-            }
-            Slot *free_slot = nullptr;
-            for (auto &sl : s->slots)
-                if (!sl.job) {
-                    free_slot = &sl;
-                    break;
+        // ---- admission (under the lock: pick jobs, reserve slot and memory) ----
+        std::vector<Start> starts;
+        if (!s->stop) {
+            const auto now = Clock::now();
+            int64_t reserve = 0;     // memory held back for an aged head job
+            for (auto it = s->queue.begin(); it != s->queue.end();) {
+                Job *j = *it;
+                if (j->cancelled) {
+                    it = s->queue.erase(it);
+                    finish(s, nullptr, j, AP_E_CANCELLED);
+                    continue;
                 }
-            if (!free_slot || s->used + j->dev_bytes > s->budget) break;
-            s->queue.pop_front();
-            j->state = Job::RUNNING;
-            free_slot->job = j;
-            s->used += j->dev_bytes;
-            s->peak = std::max(s->peak, s->used);
-            cudaError_t e = start_job(s, *free_slot, *j);
-            if (e != cudaSuccess) {
-                j->error = cudaGetErrorString(e);
-                finish(s, free_slot, j, AP_E_CUDA);
+                if (j->plan.rows == 0 || j->plan.cols == 0) {   // empty plot: nothing to run
+                    it = s->queue.erase(it);
+                    j->count = 0;
+                    finish(s, nullptr, j, AP_OK);
+                    continue;
+                }
+                Slot *free_slot = nullptr;
+                for (auto &sl : s->slots)
+                    if (!sl.job) {
+                        free_slot = &sl;
+                        break;
+                    }
+                if (!free_slot) break;
+                const bool aged = (now - j->t_submit) > kAgeLimit;
+                if (s->used + reserve + j->dev_bytes > s->budget) {
+                    if (aged && reserve == 0) reserve = j->dev_bytes;   // keep room for it
+                    ++it;
+                    continue;
+                }
+                it = s->queue.erase(it);
+                j->state = Job::RUNNING;
+                free_slot->job = j;
+                s->used += j->dev_bytes;
+                s->peak = std::max(s->peak, s->used);
+                starts.push_back({free_slot, j, cudaSuccess});
             }
         }
-        // Advance running jobs whose GPU work has finished.
-        bool progressed = false;
+        // ---- completions (event queries are cheap; the work is done unlocked) ----
+        std::vector<Done> dones;
         for (auto &sl : s->slots) {
             Job *j = sl.job;
-            if (!j) continue;
+            if (!j || j->phase == 0) continue;
             const cudaError_t q = cudaEventQuery(sl.ev);
             if (q == cudaErrorNotReady) continue;
-            progressed = true;
-            if (q != cudaSuccess) {
-                j->error = cudaGetErrorString(q);
-                finish(s, &sl, j, AP_E_CUDA);
-                continue;
-            }
-            if (j->phase == 1) {
+            dones.push_back({&sl, j, j->phase, q});
+        }
+        if (starts.empty() && dones.empty()) {
+            // Nothing to do: sleep briefly (GPU work in flight) or until a
+            // submission arrives.
+            s->cv_work.wait_for(lk, busy ? std::chrono::microseconds(50) : std::chrono::milliseconds(20));
+            continue;
+        }
+        // ---- unlocked: pinned copies, allocations, enqueues, result copies ----
+        lk.unlock();
+        for (auto &st : starts) st.err = start_job(s, *st.slot, *st.job);
+        for (auto &d : dones) {
+            if (d.err != cudaSuccess) continue;
+            Job *j = d.job;
+            Slot &sl = *d.slot;
+            if (d.phase == 1) {
                 j->count = *sl.pin_count;
                 const int64_t keep = std::min(j->count, j->max_dots);
                 cudaError_t e = grow_pinned((void **)&sl.pin_out, &sl.pin_out_cap,
                                             keep * (int64_t)sizeof(ap_dot));
                 if (e == cudaSuccess && keep > 0)
-                    e = cudaMemcpyAsync(sl.pin_out, j->dev + j->off_dots,
-                                        (size_t)keep * sizeof(ap_dot), cudaMemcpyDeviceToHost,
-                                        sl.stream);
+                    e = cudaMemcpyAsync(sl.pin_out, j->dev + j->off_dots, (size_t)keep * sizeof(ap_dot),
+                                        cudaMemcpyDeviceToHost, sl.stream);
                 if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
-                if (e != cudaSuccess) {
-                    j->error = cudaGetErrorString(e);
-                    finish(s, &sl, j, AP_E_CUDA);
-                    continue;
-                }
+                d.err = e;
                 j->phase = 2;
             } else {
                 const int64_t keep = std::min(j->count, j->max_dots);
-                if (!j->cancelled) j->result.assign(sl.pin_out, sl.pin_out + keep);
-                finish(s, &sl, j, j->count > j->max_dots ? AP_E_OVERFLOW : AP_OK);
+                j->result.assign(sl.pin_out, sl.pin_out + keep);
             }
         }
-        if (!progressed) {
-            // Nothing finished: sleep briefly (GPU work in flight) or until a
-            // submission arrives.
-            busy = false;
-            for (auto &sl : s->slots) busy |= sl.job != nullptr;
-            if (busy)
-                s->cv_work.wait_for(lk, std::chrono::microseconds(50));
-            else
-                s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        lk.lock();
+        // ---- publish (under the lock) ----
+        for (auto &st : starts)
+            if (st.err != cudaSuccess) {
+                st.job->error = cudaGetErrorString(st.err);
+                finish(s, st.slot, st.job, AP_E_CUDA);
+            }
+        for (auto &d : dones) {
+            Job *j = d.job;
+            if (d.err != cudaSuccess) {
+                j->error = cudaGetErrorString(d.err);
+                finish(s, d.slot, j, AP_E_CUDA);
+            } else if (d.phase == 2) {
+                if (j->cancelled) j->result.clear();
+                finish(s, d.slot, j, j->count > j->max_dots ? AP_E_OVERFLOW : AP_OK);
+            }
         }
     }
 }

@@ -9,6 +9,10 @@ if ROOT not in sys.path:
 
 
 def pytest_configure(config):
+    # the batch autotuner's persistent cache: tests keep theirs apart from a
+    # user's (and from a benchmark run after them)
+    import tempfile
+    os.environ.setdefault("AP_TUNE_CACHE", os.path.join(tempfile.mkdtemp(prefix="alnplot-tests-"), "tune.txt"))
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the CUDA path)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
 

@@ -166,3 +166,9 @@ def test_band_rows_override_sets_the_banded_workspaces():
     with pytest.raises(ap.ApError) as e:
         ap.set_band_rows(-1)
     assert e.value.status == ap.AP_E_INVAL
+
+
+def test_release_build_has_no_bounds_checks():
+    with pytest.raises(ap.ApError) as e:
+        ap.debug_bounds()
+    assert e.value.status == ap.AP_E_UNSUPPORTED

@@ -282,6 +282,10 @@ STEP_CASES = [
     (300, 260, 16, 2, (1, 0, 0)), (333, 290, 30, 5, (1, 0, 0)), (500, 410, 64, 3, (1, 0, 0)),
     (600, 500, 100, 5, (1, 0, 0)), (420, 380, 120, 7, (1, 0, 0)), (250, 300, 20, 5, (2, 1, 0)),
     (500, 430, 100, 5, (2, 1, 0)), (37, 60, 9, 4, (1, 0, 0)),
+    # wide windows: full 8-bit keys, 16-bit lanes ({2,1,0} above w = 120)
+    (500, 450, 150, 3, (1, 0, 0)), (600, 520, 200, 5, (1, 0, 0)), (620, 600, 128, 7, (1, 0, 0)),
+    (700, 640, 256, 4, (1, 0, 0)), (800, 700, 300, 5, (1, 0, 0)), (900, 760, 480, 5, (1, 0, 0)),
+    (600, 640, 200, 2, (2, 1, 0)), (700, 600, 150, 3, (2, 1, 0)), (720, 700, 256, 6, (2, 1, 0)),
 ]
 
 
