@@ -1356,10 +1356,13 @@ __device__ __forceinline__ bool build_tables_g(const CombParams &p, int64_t iw, 
 }
 
 // One comb cell with the match folded in by a table word (see above; X & pk
-// is the no-match word in padding rows).
+// is the no-match word in padding rows).  FMA_HN forms the right output as
+// (h + v) - bottom on the FMA pipe, as cell_tab does (not for full 8-bit
+// keys, whose lane sums would carry).
 template <class L>
 __device__ __forceinline__ void cell_tx(uint32_t &h, uint32_t &v, uint32_t X, uint32_t pk,
-                                        uint32_t neg1, uint32_t sph, uint32_t spl)
+                                        uint32_t neg1, uint32_t sph, uint32_t spl,
+                                        bool FMA_HN = false, uint32_t one = 1u)
 {
     uint32_t M;
     if (L::FULL) {
@@ -1371,9 +1374,16 @@ __device__ __forceinline__ void cell_tx(uint32_t &h, uint32_t &v, uint32_t X, ui
         M = spread<L>(t, sph, spl);
     }
     const uint32_t vn = (h & M) | (v & ~M);
-    h = h ^ v ^ vn;
+    if (FMA_HN && !L::FULL) h = mad_lo(vn, neg1, mad_lo(h, one, v));
+    else h = h ^ v ^ vn;
     v = vn;
 }
+
+#ifndef AP_TABG_HNF
+// Right output of the second column of each step on the FMA pipe in the
+// G > 1 table path (16-bit lanes; full 8-bit keys keep the logic form).
+#define AP_TABG_HNF 1
+#endif
 
 // The LCS comb of one tile through per-g tables, rows split over G > 1
 // threads with the skewed wavefront of comb_tile: the same method, window
@@ -1527,7 +1537,7 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
                 const int pi = k - (R - PADU);
                 const uint32_t kp = (pi >= 0) ? pk[pi < 0 ? 0 : pi] : 0xFFFFFFFFu;
                 cell_tx<L>(h[k], va, X0[r], kp, neg1, sph, spl);
-                cell_tx<L>(h[k], vb, X1[r], kp, neg1, sph, spl);
+                cell_tx<L>(h[k], vb, X1[r], kp, neg1, sph, spl, AP_TABG_HNF != 0, one);
             }
         }
         vdown[0] = va;
