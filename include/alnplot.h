@@ -147,6 +147,16 @@ ap_status ap_set_chunk(int64_t chunk);
 ap_status ap_set_band_rows(int64_t rows);
 
 /*
+ * Tuning: ask for a lane format of the LCS comb -- 8 (four strips per
+ * register; windows up to 254), 10 (three strips; 121..480) or 16 bits (two
+ * strips; any window up to 512) -- for later plot and dots calls in this
+ * process; 0 restores the automatic choice.  Honoured where the format
+ * covers the window, else the automatic choice is used.  Results do not
+ * depend on it.  Process-wide; AP_E_INVAL unless bits is 0, 8, 10 or 16.
+ */
+ap_status ap_set_lane_bits(int32_t bits);
+
+/*
  * Tuning: ask for `groups` threads per group of strips (the comb rows of one
  * strip are split over them; 0 restores the automatic choice).  Honoured
  * when a compiled variant exists for the window length, else the automatic

@@ -19,7 +19,7 @@ import threading
 
 __all__ = [
     "load", "ApError", "LCS", "SCORE", "plot_shape", "plot_plan", "alignment_plot",
-    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "alignment_plot_step", "alignment_plot_host", "set_chunk", "set_band_rows", "set_lanes_per_strip", "Batch", "Server", "DOT_DTYPE_FIELDS",
+    "alignment_dots", "plot_dots", "plot_checksum", "empty_plot", "version", "alignment_plot_step", "alignment_plot_host", "set_chunk", "set_band_rows", "set_lane_bits", "set_lanes_per_strip", "Batch", "Server", "DOT_DTYPE_FIELDS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -98,6 +98,7 @@ def _declare(lib):
         "ap_set_chunk": [i64],
         "ap_set_lanes_per_strip": [i32],
         "ap_set_band_rows": [i64],
+        "ap_set_lane_bits": [i32],
         "ap_plot_shape": [i64, i64, i32, i64p, i64p],
         "ap_plot_plan": [i64, i64, i32, sc, ctypes.POINTER(ap_plan)],
         "ap_alignment_plot": [p, i64, p, i64, i32, sc, p, i32, i64, p],
@@ -196,6 +197,12 @@ def set_band_rows(rows: int) -> None:
     """Force the band height (plot rows) of the banded calls -- dots, plots
     into host memory, server jobs (0 = automatic); results do not change."""
     _check(load().ap_set_band_rows(int(rows)))
+
+
+def set_lane_bits(bits: int) -> None:
+    """Ask for a lane format of the LCS comb (0 = automatic, 8, 10 or 16
+    bits); results do not change."""
+    _check(load().ap_set_lane_bits(int(bits)))
 
 
 def set_lanes_per_strip(groups: int) -> None:

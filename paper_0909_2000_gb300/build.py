@@ -48,11 +48,13 @@ def _variants():
     for r in range(32, 65, 4):
         v.append(("U8FLanes", 8, 8, r, 4, 1, 0, 8))
     # LCS, 9-bit keys in 10-bit lanes (three strips per register), rows split
-    # over 4 or 8 threads: 256 < w <= 480
-    for r in range(66, 97, 3):
+    # over 4 or 8 threads: 256 < w <= 480 by default, 120 < w on request
+    # (measured slower than full 8-bit keys and 16-bit lanes up to w = 256)
+    for r in range(33, 97, 3):
         v.append(("U10Lanes", 9, 10, r, 4, 1, 0, 8))
     for r in range(33, 61, 3):
         v.append(("U10Lanes", 9, 10, r, 8, 1, 0, 8))
+
     # LCS, 15-bit keys in 16-bit lanes, rows split over 2, 4 or 8 threads: w <= 512
     for g in (2, 4, 8):
         for r in range(16, 65, 8):

@@ -15,6 +15,7 @@ static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_chunk_override{0};
 static std::atomic<int32_t> g_groups_override{0};
 static std::atomic<int64_t> g_band_override{0};
+static std::atomic<int32_t> g_lane_override{0};
 
 int64_t band_rows_override() { return g_band_override.load(); }
 
@@ -126,7 +127,8 @@ namespace {
 ap_status make_plan(int64_t m, int64_t n, int32_t w, const ap_scores *scores, Plan *pl,
                     int64_t step = 1)
 {
-    return plan_plot(m, n, w, scores, g_groups_override.load(), g_chunk_override.load(), pl, step);
+    return plan_plot(m, n, w, scores, g_groups_override.load(), g_chunk_override.load(), pl, step,
+                     g_lane_override.load());
 }
 
 constexpr int64_t kBandBudget = 1LL << 30;   // bytes of banded plot per dots pass
@@ -192,6 +194,14 @@ ap_status ap_set_band_rows(int64_t rows)
 {
     if (rows < 0) return fail(AP_E_INVAL, "band rows = %lld: must be >= 0", (long long)rows);
     g_band_override.store(rows);
+    return AP_OK;
+}
+
+ap_status ap_set_lane_bits(int32_t bits)
+{
+    if (bits != 0 && bits != 8 && bits != 10 && bits != 16)
+        return fail(AP_E_INVAL, "lane bits = %d: must be 0 (automatic), 8, 10 or 16", bits);
+    g_lane_override.store(bits);
     return AP_OK;
 }
 

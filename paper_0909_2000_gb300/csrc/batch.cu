@@ -318,8 +318,7 @@ ap_status tune_class(ap_batch *b, const std::vector<int> &idx, int nu, int w, Sc
                 saved.push_back(b->plans[j]);
                 const ap_job &jb = b->jobs[j];
                 ap_status s = plan_plot(jb.m, jb.n, jb.w, &jb.scores, gc, cc, &b->plans[j], 1, lb);
-                if (s != AP_OK) {
-                    st = s;
+                if (s != AP_OK) {             // a request the planner cannot serve
                     match = false;
                     break;
                 }
@@ -328,7 +327,6 @@ ap_status tune_class(ap_batch *b, const std::vector<int> &idx, int nu, int w, Sc
             }
             if (!match) {                  // no compiled variant for this request
                 for (size_t k = 0; k < saved.size(); ++k) b->plans[sample[k]] = saved[k];
-                if (st != AP_OK) break;
                 continue;
             }
             Group g;

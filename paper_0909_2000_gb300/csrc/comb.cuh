@@ -1247,7 +1247,13 @@ __host__ __device__ constexpr int tabg_words(int ns, int g, int r)
 
 __host__ __device__ constexpr bool has_tables_g(int key_bits, int groups, int nu, bool xrows)
 {
-    return nu == 1 && !xrows && groups > 1 && (key_bits == 8 || key_bits == 15);
+    return nu == 1 && !xrows && groups > 1 && (key_bits == 8 || key_bits == 9 || key_bits == 15);
+}
+
+// Strips per register of a lane width (8, 10 or 16 bits).
+__host__ __device__ constexpr int lane_strips(int lane_bits)
+{
+    return lane_bits == 8 ? 4 : (lane_bits == 10 ? 3 : 2);
 }
 
 // First row of thread g's share (g = G: the window w).
@@ -1381,7 +1387,8 @@ __device__ __forceinline__ void cell_tx(uint32_t &h, uint32_t &v, uint32_t X, ui
 
 #ifndef AP_TABG_HNF
 // Right output of the second column of each step on the FMA pipe in the
-// G > 1 table path (16-bit lanes; full 8-bit keys keep the logic form).
+// G > 1 table path (16- and 10-bit lanes, whose key sums fit their lanes;
+// full 8-bit keys keep the logic form).
 #define AP_TABG_HNF 1
 #endif
 
@@ -1570,7 +1577,7 @@ __device__ __forceinline__ void comb_tile_dispatch(const CombParams &p, int64_t 
 {
     constexpr bool FAST_OK = L::BITS == 8;
     constexpr bool TAB = L::BITS == 8 && !L::FULL && has_tables(7, G, NU, XR);
-    constexpr bool TABG = has_tables_g(L::BITS == 16 ? 15 : (L::FULL ? 8 : 0), G, NU, XR);
+    constexpr bool TABG = has_tables_g(L::BITS == 16 ? 15 : (L::BITS == 10 ? 9 : (L::FULL ? 8 : 0)), G, NU, XR);
     if constexpr (TAB) {
         uint32_t *tab = ring + p.ring * (32 / G) + kOB * (32 / G + 1);
         if (build_tables<R>(p, sg * 128, tab, threadIdx.x & 31)) {

@@ -26,6 +26,18 @@ const Variant *find_variant(int key_bits, int rows, int groups, int nu, int mu, 
     return nullptr;
 }
 
+// A variant can comb window w only if each thread's share of the strip's
+// units (rows, or characters of a blow-up) fits its compiled rows and the
+// rows left over fit its padding window: the kernels mask only the last
+// PADU units of each thread as never-matching rows.
+bool padding_ok(const Variant *v, int w)
+{
+    const int units = v->rows / v->nu;          // units per thread
+    const int lo = w / v->groups;               // smallest share (even split)
+    const int hi = (w + v->groups - 1) / v->groups;
+    return hi <= units && units - lo <= v->padu;
+}
+
 int next_pow2(int v)
 {
     int p = 1;
@@ -80,7 +92,7 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
         // format covers w: 8-bit lanes up to 254, 10-bit lanes for 257..480,
         // 16-bit lanes always; otherwise the default below.
         const bool want16 = want_lane_bits == 16 && w <= 512;
-        const bool want10 = want_lane_bits == 10 && w > 256 && w <= 480;
+        const bool want10 = want_lane_bits == 10 && w > 120 && w <= 480;
         if (want16) {
             kbits = 15;
             if (want_groups == 2 || want_groups == 4 || want_groups == 8)
@@ -90,7 +102,8 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
                     if (rows_for(g, 8, 16, 64)) break;
         } else if (want10) {
             kbits = 9;
-            if (want_groups == 8 || !rows_for(4, 3, 66, 96)) rows_for(8, 3, 33, 60);
+            if (want_groups != 8) rows_for(4, 3, 33, 96);
+            if (!rows) rows_for(8, 3, 33, 60);
         } else if (w <= 120) {
             kbits = 7;
             if (want_groups == 2) rows_for(2, 4, 16, 60);
@@ -140,6 +153,9 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
         }
     }
     const Variant *v = (rows > 0) ? find_variant(kbits, rows, groups, nu, mu, xrows) : nullptr;
+    if (v && !padding_ok(v, w)) v = nullptr;
+    if (!v && (want_groups > 0 || want_lane_bits > 0))   // a request no variant serves:
+        return choose_variant(w, nu, mu, 0, step, pl, why, 0);   // the automatic choice
     if (!v) {
         if (why) {
             char buf[160];
@@ -182,7 +198,7 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
     pl->warp_words = pl->ring * ngrp + kOB * (ngrp + 1);
     if (has_tables(v->key_bits, v->groups, v->nu, v->xrows != 0)) pl->warp_words += tab_words(v->rows);
     if (has_tables_g(v->key_bits, v->groups, v->nu, v->xrows != 0))
-        pl->warp_words += tabg_words(v->lane_bits == 8 ? 4 : 2, v->groups, v->rows);
+        pl->warp_words += tabg_words(lane_strips(v->lane_bits), v->groups, v->rows);
     pl->smem = (size_t)kWarpsPerBlock * (size_t)pl->warp_words * 4u;
     return true;
 }
@@ -325,7 +341,7 @@ void fill_params(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y, 
     p->scale = (uint32_t)pl.scale;
     const Variant *v = pl.v;
     p->tab = has_tables_g(v->key_bits, v->groups, v->nu, v->xrows != 0) &&
-             tabg_split_ok(pl.w, v->groups, v->rows, tabg_rpl(v->lane_bits == 8 ? 4 : 2), v->padu);
+             tabg_split_ok(pl.w, v->groups, v->rows, tabg_rpl(lane_strips(v->lane_bits)), v->padu);
     p->dbg = debug_flags();
 }
 

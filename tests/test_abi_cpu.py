@@ -172,3 +172,37 @@ def test_release_build_has_no_bounds_checks():
     with pytest.raises(ap.ApError) as e:
         ap.debug_bounds()
     assert e.value.status == ap.AP_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("bits,g,w", [(10, 4, 128), (10, 4, 200), (16, 4, 128), (8, 4, 200), (16, 8, 100)])
+def test_lane_format_switch(bits, g, w):
+    try:
+        ap.set_lane_bits(bits)
+        ap.set_lanes_per_strip(g)
+        pl = ap.plot_plan(w + 500, w + 400, w)
+    finally:
+        ap.set_lane_bits(0)
+        ap.set_lanes_per_strip(0)
+    assert pl["lane_bits"] == bits and pl["lanes_per_strip"] == g
+    assert pl["rows_per_lane"] * g >= w
+    with pytest.raises(ap.ApError):
+        ap.set_lane_bits(12)
+
+
+@pytest.mark.parametrize("w", [1, 5, 10, 15, 16, 40, 100, 128, 200, 256, 300, 480])
+@pytest.mark.parametrize("bits", [0, 8, 10, 16])
+@pytest.mark.parametrize("g", [0, 1, 2, 4, 8])
+def test_requested_layouts_keep_padding_within_the_masked_rows(w, bits, g):
+    """Any lane-format and threads-per-strip request yields a plan whose
+    threads each hold their share of the window with at most the masked
+    padding rows (else the automatic choice): rows_per_lane * groups covers
+    w, and no thread's share falls more than 8 rows short of its rows."""
+    try:
+        ap.set_lane_bits(bits)
+        ap.set_lanes_per_strip(g)
+        pl = ap.plot_plan(w + 700, w + 600, w)
+    finally:
+        ap.set_lane_bits(0)
+        ap.set_lanes_per_strip(0)
+    G, R = pl["lanes_per_strip"], pl["rows_per_lane"]
+    assert R * G >= w and R - w // G <= 8, pl

@@ -136,6 +136,36 @@ def test_scaled_and_wide_score_schemes(cuda_lib, m, n, w, scores):
     assert count == len(want) and np.array_equal(ap.dots_to_numpy(dots, count), want)
 
 
+# Every lane format at windows it shares with the others (ap_set_lane_bits):
+# 8-bit full keys, 10-bit lanes and 16-bit lanes on 2, 4 and 8 threads, DNA
+# (table paths) and 20 letters (general paths).
+LANE_CASES = [(bits, g, w, alph) for bits, g, w in
+              [(10, 4, 121), (10, 4, 128), (10, 4, 129), (10, 4, 200), (10, 4, 256), (10, 8, 250),
+               (16, 2, 126), (16, 4, 200), (16, 8, 254), (8, 2, 127), (8, 4, 201)]
+              for alph in (b"ACGT", b"ACDEFGHIKLMNPQRSTVWY")]
+
+
+@pytest.mark.parametrize("bits,g,w,alph", LANE_CASES)
+def test_lane_formats_at_shared_windows(cuda_lib, bits, g, w, alph):
+    ap = cuda_lib
+    seed = bits * 1000 + g * 100 + w
+    x = synth.alphabet_string(seed, 1, w + 230, np.frombuffer(alph, np.uint8))
+    y = synth.alphabet_string(seed, 2, w + 310, np.frombuffer(alph, np.uint8))
+    if alph == b"ACGT":
+        y, _ = synth.plant(x, y, 1, 150, seed, 3, synth.DNA, 0.1, 0.05)
+    o = oracle.plot(x, y, w)
+    try:
+        ap.set_lane_bits(bits)
+        ap.set_lanes_per_strip(g)
+        pl = ap.plot_plan(len(x), len(y), w)
+        assert pl["lane_bits"] == bits and pl["lanes_per_strip"] == g, pl
+        got = gpu_plot(ap, x, y, w, (1, 0, 0), torch.int16) & 0xFFFF
+    finally:
+        ap.set_lane_bits(0)
+        ap.set_lanes_per_strip(0)
+    assert got.shape == o.shape and np.array_equal(got, o), np.argwhere(got != o)[:4].tolist()
+
+
 @pytest.mark.parametrize("w,scores", [(9, (1, 0, 0)), (100, (1, 0, 0)), (150, (1, 0, 0)),
                                       (300, (1, 0, 0)), (20, (2, 1, 0)), (90, (2, 1, 0)),
                                       (140, (2, 1, 0))])
@@ -326,3 +356,19 @@ def test_plot_into_host_memory(cuda_lib, m, n, w, thr, scores):
         assert np.array_equal(out.numpy().astype(np.int64), oracle.plot(x, y, w, scores[0], scores[1]))
     plot_only, _, _ = ap.alignment_plot_host(x, y, w, scores)
     assert torch.equal(plot_only, out)
+
+
+@pytest.mark.parametrize("bits,g,w", [(0, 2, 10), (0, 2, 15), (10, 8, 128), (16, 8, 40), (16, 2, 9)])
+def test_requests_no_variant_serves_fall_back(cuda_lib, bits, g, w):
+    """Requests whose variant would leave a thread more unmasked padding rows
+    than it masks take the automatic plan, and plot correctly."""
+    ap = cuda_lib
+    x, y = synth.dna(w, 1, w + 260), synth.dna(w, 2, w + 300)
+    try:
+        ap.set_lane_bits(bits)
+        ap.set_lanes_per_strip(g)
+        got = gpu_plot(ap, x, y, w, (1, 0, 0), torch.int16) & 0xFFFF
+    finally:
+        ap.set_lane_bits(0)
+        ap.set_lanes_per_strip(0)
+    assert np.array_equal(got, oracle.plot(x, y, w))
