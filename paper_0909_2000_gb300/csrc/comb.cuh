@@ -935,18 +935,27 @@ __host__ __device__ constexpr bool has_tables(int key_bits, int groups, int nu, 
 }
 
 #ifndef AP_TAB_CPS
-#define AP_TAB_CPS 2   // plot columns per step of the table path (2 or 4)
+#define AP_TAB_CPS 2   // plot columns per step of the table path (2 to 4)
+#endif
+#ifndef AP_TAB_SEL
+// 1: the one-thread tables hold byte-permute selectors (match: take 0xFF from
+// a constant; mismatch: spread the compare's sign bit) instead of OR masks,
+// so that h | 0x80 becomes a multiply-add and the cell has one logic
+// instruction fewer (see cell_sel).  Measured on the 100k DNA plot, w = 100,
+// comb alone: 59.3 ms, against 62.2 ms for OR masks.
+#define AP_TAB_SEL 1
 #endif
 #ifndef AP_TAB_HNF
-// Columns of each step whose right output is formed on the FMA pipe: one of
-// the two measured 62.2 ms against 65.3 ms for none and 65.9 ms for both
-// (100k DNA, w = 100, comb alone).
-#define AP_TAB_HNF 1
+// Columns of each step whose right output is formed on the FMA pipe.  With OR
+// masks one of the two was best (62.2 ms against 65.3 ms for none and 65.9 ms
+// for both); with selectors, whose h + 0x80.. already runs on the FMA pipe,
+// none (59.3 ms against 65.5 ms for one and 71.2 ms for both).
+#define AP_TAB_HNF 0
 #endif
 
 // Builds the warp's tables; false (warp-uniform) if the x characters of the
 // warp take more than kTabSyms values.
-template <int R>
+template <int R, bool SEL = false>
 __device__ __forceinline__ bool build_tables(const CombParams &p, int64_t iw, uint32_t *tab,
                                              int lane)
 {
@@ -1003,10 +1012,14 @@ __device__ __forceinline__ bool build_tables(const CombParams &p, int64_t iw, ui
             const uint32_t c = sym[s];
             uint32_t wv = 0u;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) wv |= ((in[b] && ch[b] == c) ? 0xFFu : 0x80u) << (8 * b);
+            for (int b = 0; b < 4; ++b) {
+                const bool hit = in[b] && ch[b] == c;
+                if (SEL) wv |= (hit ? 4u + b : 8u + b) << (4 * b);     // selector nibble of lane b
+                else wv |= (hit ? 0xFFu : 0x80u) << (8 * b);
+            }
             tb[s * P + q] = wv;
         }
-        tb[kTabSyms * P + q] = 0x80808080u;
+        tb[kTabSyms * P + q] = SEL ? 0xBA98u : 0x80808080u;
     }
     __syncwarp();
     return true;
@@ -1024,6 +1037,22 @@ __device__ __forceinline__ void cell_tab(uint32_t &h, uint32_t &v, uint32_t X, u
     const uint32_t hc = h | (X & pk);
     const uint32_t t = mad_lo(v, neg1, hc);                 // hc - v
     const uint32_t M = prmt(t, 0u, U8Lanes::SIGNREP);
+    const uint32_t vn = (h & M) | (v & ~M);
+    if (FMA_HN) h = mad_lo(vn, neg1, mad_lo(h, one, v));
+    else h = h ^ v ^ vn;
+    v = vn;
+}
+
+// One comb cell with the match folded into the byte permute (selector tables,
+// AP_TAB_SEL): t = (h + 0x80..) - v on the FMA pipe gives h >= v in each
+// lane's top bit (keys are 7 bits: no carry or borrow crosses a lane); the
+// selector S takes 0xFF from `ones` in match lanes and spreads t's sign bit
+// in mismatch lanes, so M is the swap mask of cell_tab.
+__device__ __forceinline__ void cell_sel(uint32_t &h, uint32_t &v, uint32_t S, uint32_t one,
+                                         uint32_t neg1, uint32_t c80, bool FMA_HN)
+{
+    const uint32_t t = mad_lo(v, neg1, mad_lo(h, one, c80));
+    const uint32_t M = prmt(t, 0xFFFFFFFFu, S);
     const uint32_t vn = (h & M) | (v & ~M);
     if (FMA_HN) h = mad_lo(vn, neg1, mad_lo(h, one, v));
     else h = h ^ v ^ vn;
@@ -1049,7 +1078,7 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
 // 7-bit keys in 8-bit lanes).  The same method, window count and output as
 // comb_tile; CPS plot columns per step (CPS independent dependency chains per
 // thread), each column's row words read from the table of its y character.
-template <int R, int PADU, int CPS, int HNF>
+template <int R, int PADU, int CPS, int HNF, bool SEL = false>
 __device__ __forceinline__ void comb_tile_tab(const CombParams &p, int64_t sg, int64_t ch,
                                               uint32_t *ring, const uint32_t *tab)
 {
@@ -1059,7 +1088,7 @@ __device__ __forceinline__ void comb_tile_tab(const CombParams &p, int64_t sg, i
     constexpr int SPW = NGRP * NS;
     constexpr int P = tab_positions(R);
     static_assert(R % 4 == 0, "rows in whole x words");
-    static_assert(CPS == 2 || CPS == 4, "two or four columns per step");
+    static_assert(CPS >= 2 && CPS <= 4, "two to four columns per step");
     static_assert(PADU <= R, "padding window larger than the lane");
 
     const int lane = threadIdx.x & 31;
@@ -1072,9 +1101,13 @@ __device__ __forceinline__ void comb_tile_tab(const CombParams &p, int64_t sg, i
     const int64_t c1 = (c0 + p.chunk < p.cols) ? c0 + p.chunk : p.cols;
     const int wk = p.w;
 
+    // padding rows never match: OR masks are ANDed with the no-match word,
+    // selectors replaced by the all-mismatch selector (pk = 0 in those rows)
     uint32_t pk[PADU > 0 ? PADU : 1];
 #pragma unroll
-    for (int t = 0; t < PADU; ++t) pk[t] = ((R - PADU + t) >= wk) ? 0x80808080u : 0xFFFFFFFFu;
+    for (int t = 0; t < PADU; ++t)
+        pk[t] = ((R - PADU + t) >= wk) ? (SEL ? 0u : 0x80808080u) : 0xFFFFFFFFu;
+    const uint32_t c80 = 0x80808080u;
 
     for (int e = lane; e < p.ring * NGRP; e += 32) ring[e] = 0u;
     __syncwarp();
@@ -1166,7 +1199,8 @@ __device__ __forceinline__ void comb_tile_tab(const CombParams &p, int64_t sg, i
 #pragma unroll
             for (int c = 0; c < CPS; ++c) {
                 const uint32_t a = tcol[c] + 16u * (uint32_t)j;
-                X[c] = AP_CHECK(p, a >= tlo && a + 16u <= thi, kDbgTable) ? lds128(a) : make_uint4(0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u);
+                const uint32_t nm = SEL ? 0xBA98u : 0x80808080u;   // the no-match word
+                X[c] = AP_CHECK(p, a >= tlo && a + 16u <= thi, kDbgTable) ? lds128(a) : make_uint4(nm, nm, nm, nm);
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -1176,7 +1210,11 @@ __device__ __forceinline__ void comb_tile_tab(const CombParams &p, int64_t sg, i
 #pragma unroll
                 for (int c = 0; c < CPS; ++c) {
                     const uint32_t xv = r == 0 ? X[c].x : (r == 1 ? X[c].y : (r == 2 ? X[c].z : X[c].w));
-                    cell_tab(h[k], v[c], xv, kp, one, neg1, c < HNF);
+                    if (SEL)
+                        cell_sel(h[k], v[c], pi >= 0 ? ((xv & kp) | (0xBA98u & ~kp)) : xv, one, neg1, c80,
+                                 c < HNF);
+                    else
+                        cell_tab(h[k], v[c], xv, kp, one, neg1, c < HNF);
                 }
             }
         }
@@ -1256,6 +1294,26 @@ __host__ __device__ constexpr int lane_strips(int lane_bits)
     return lane_bits == 8 ? 4 : (lane_bits == 10 ? 3 : 2);
 }
 
+// The table word of a lane format: OR masks (match: the whole lane; no
+// match: 0 for full 8-bit keys, the lane's top bit otherwise) or
+// byte-permute selectors (match: bytes of the all-ones constant; no match:
+// the lane's sign spread over its bytes).
+template <class L, bool SEL>
+__host__ __device__ constexpr uint32_t tab_lane_word(bool hit, int b)
+{
+    if (!SEL) return hit ? (L::MASK << (L::BITS * b)) : (L::FULL ? 0u : (L::MSB & (L::MASK << (L::BITS * b))));
+    if (L::BITS == 8) return (uint32_t)(hit ? 4 + b : 8 + b) << (4 * b);
+    // 16-bit lane b: bytes 2b, 2b + 1
+    return hit ? (0x44u << (8 * b)) : ((uint32_t)((8 + 2 * b + 1) * 0x11) << (8 * b));
+}
+
+// The no-match word of a whole register.
+template <class L, bool SEL>
+__host__ __device__ constexpr uint32_t tab_nomatch()
+{
+    return SEL ? (L::BITS == 8 ? 0xBA98u : 0xBB99u) : (L::FULL ? 0u : L::MSB);
+}
+
 // First row of thread g's share (g = G: the window w).
 __host__ __device__ inline int tabg_ub(int w, int G, int rpl, int g)
 {
@@ -1288,7 +1346,7 @@ __device__ __forceinline__ void lds_rows(uint32_t saddr, uint32_t *out)
 
 // Builds the tables of a G > 1 warp; false (warp-uniform) if its x
 // characters take more than kTabSyms values.
-template <class L, int G, int R>
+template <class L, int G, int R, bool SEL = false>
 __device__ __forceinline__ bool build_tables_g(const CombParams &p, int64_t iw, uint32_t *tab,
                                                int lane)
 {
@@ -1333,7 +1391,6 @@ __device__ __forceinline__ bool build_tables_g(const CombParams &p, int64_t iw, 
         if (present) sym[rank] = (uint8_t)c;
     }
     __syncwarp();
-    const uint32_t nomatch = L::FULL ? 0u : L::MSB;
     for (int g = 0; g < G; ++g) {
         const int ub = tabg_ub(wk, G, RPL, g);
         uint32_t *copy = tab + g * S;
@@ -1348,13 +1405,12 @@ __device__ __forceinline__ bool build_tables_g(const CombParams &p, int64_t iw, 
             }
             for (int s = 0; s < total; ++s) {
                 const uint32_t c = sym[s];
-                uint32_t wv = nomatch;
+                uint32_t wv = 0u;
 #pragma unroll
-                for (int b = 0; b < NS; ++b)
-                    if (in[b] && ch[b] == c) wv |= L::MASK << (L::BITS * b);
+                for (int b = 0; b < NS; ++b) wv |= tab_lane_word<L, SEL>(in[b] && ch[b] == c, b);
                 copy[s * Q + q] = wv;
             }
-            copy[kTabSyms * Q + q] = nomatch;
+            copy[kTabSyms * Q + q] = tab_nomatch<L, SEL>();
         }
     }
     __syncwarp();
@@ -1385,6 +1441,35 @@ __device__ __forceinline__ void cell_tx(uint32_t &h, uint32_t &v, uint32_t X, ui
     v = vn;
 }
 
+// One comb cell with the match folded into the byte permute (selector
+// tables): as cell_sel, for 16-bit lanes (h + 0x8000.. - v on the FMA pipe)
+// and for full 8-bit keys (the full-width compare of h and v, whose result
+// the selector overrides in match lanes).
+template <class L>
+__device__ __forceinline__ void cell_txs(uint32_t &h, uint32_t &v, uint32_t S, uint32_t neg1,
+                                         uint32_t one, bool FMA_HN)
+{
+    uint32_t M;
+    if (L::FULL) {
+        M = prmt(ge_lanes<L>(h, v, neg1), 0xFFFFFFFFu, S);
+    } else {
+        const uint32_t t = mad_lo(v, neg1, mad_lo(h, one, L::MSB));
+        M = prmt(t, 0xFFFFFFFFu, S);
+    }
+    const uint32_t vn = (h & M) | (v & ~M);
+    if (FMA_HN && !L::FULL) h = mad_lo(vn, neg1, mad_lo(h, one, v));
+    else h = h ^ v ^ vn;
+    v = vn;
+}
+
+#ifndef AP_TABG_SEL
+// 1: the G > 1 tables of full 8-bit keys hold byte-permute selectors instead
+// of OR masks (see cell_txs): measured on the 100k DNA plot, w = 128, comb
+// alone, 132.3 ms against 148.8 ms.  16-bit lanes keep OR masks (selectors:
+// 380.6 ms against 373.0 at w = 256), and 10-bit lanes, which spread their
+// compare bits with multiplies, too.
+#define AP_TABG_SEL 1
+#endif
 #ifndef AP_TABG_HNF
 // Right output of the second column of each step on the FMA pipe in the
 // G > 1 table path (16- and 10-bit lanes, whose key sums fit their lanes;
@@ -1396,7 +1481,7 @@ __device__ __forceinline__ void cell_tx(uint32_t &h, uint32_t &v, uint32_t X, ui
 // threads with the skewed wavefront of comb_tile: the same method, window
 // count and output; only the row masks come from the tables and the split
 // is the aligned one.
-template <class L, int R, int G, int PADU>
+template <class L, int R, int G, int PADU, bool SEL = false>
 __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, int64_t ch,
                                                uint32_t *ring, const uint32_t *tab)
 {
@@ -1421,10 +1506,13 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
     const int wk = p.w;
     const int nreal = tabg_ub(wk, G, RPL, g + 1) - tabg_ub(wk, G, RPL, g);
 
-    const uint32_t nomatch = L::FULL ? 0u : L::MSB;
+    const uint32_t nomatch = tab_nomatch<L, SEL>();
+    // padding rows never match: OR masks are ANDed with the no-match word;
+    // selectors are replaced by it (pk = 0 in those rows)
     uint32_t pk[PADU > 0 ? PADU : 1];
 #pragma unroll
-    for (int t = 0; t < PADU; ++t) pk[t] = ((R - PADU + t) >= nreal) ? nomatch : 0xFFFFFFFFu;
+    for (int t = 0; t < PADU; ++t)
+        pk[t] = ((R - PADU + t) >= nreal) ? (SEL ? 0u : nomatch) : 0xFFFFFFFFu;
 
     for (int e = lane; e < p.ring * NGRP; e += 32) ring[e] = 0u;
     __syncwarp();
@@ -1543,8 +1631,15 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
                 const int k = RPL * j + r;
                 const int pi = k - (R - PADU);
                 const uint32_t kp = (pi >= 0) ? pk[pi < 0 ? 0 : pi] : 0xFFFFFFFFu;
-                cell_tx<L>(h[k], va, X0[r], kp, neg1, sph, spl);
-                cell_tx<L>(h[k], vb, X1[r], kp, neg1, sph, spl, AP_TABG_HNF != 0, one);
+                if (SEL) {
+                    const uint32_t s0 = pi >= 0 ? ((X0[r] & kp) | (nomatch & ~kp)) : X0[r];
+                    const uint32_t s1 = pi >= 0 ? ((X1[r] & kp) | (nomatch & ~kp)) : X1[r];
+                    cell_txs<L>(h[k], va, s0, neg1, one, false);
+                    cell_txs<L>(h[k], vb, s1, neg1, one, AP_TABG_HNF != 0);
+                } else {
+                    cell_tx<L>(h[k], va, X0[r], kp, neg1, sph, spl);
+                    cell_tx<L>(h[k], vb, X1[r], kp, neg1, sph, spl, AP_TABG_HNF != 0, one);
+                }
             }
         }
         vdown[0] = va;
@@ -1580,15 +1675,16 @@ __device__ __forceinline__ void comb_tile_dispatch(const CombParams &p, int64_t 
     constexpr bool TABG = has_tables_g(L::BITS == 16 ? 15 : (L::BITS == 10 ? 9 : (L::FULL ? 8 : 0)), G, NU, XR);
     if constexpr (TAB) {
         uint32_t *tab = ring + p.ring * (32 / G) + kOB * (32 / G + 1);
-        if (build_tables<R>(p, sg * 128, tab, threadIdx.x & 31)) {
-            comb_tile_tab<R, PADU, AP_TAB_CPS, AP_TAB_HNF>(p, sg, ch, ring, tab);
+        if (build_tables<R, AP_TAB_SEL != 0>(p, sg * 128, tab, threadIdx.x & 31)) {
+            comb_tile_tab<R, PADU, AP_TAB_CPS, AP_TAB_HNF, AP_TAB_SEL != 0>(p, sg, ch, ring, tab);
             return;
         }
     }
     if constexpr (TABG) {
         uint32_t *tab = ring + p.ring * (32 / G) + kOB * (32 / G + 1);
-        if (p.tab && build_tables_g<L, G, R>(p, sg * (32 / G) * L::NS, tab, threadIdx.x & 31)) {
-            comb_tile_tabg<L, R, G, PADU>(p, sg, ch, ring, tab);
+        constexpr bool TSEL = AP_TABG_SEL != 0 && L::FULL;
+        if (p.tab && build_tables_g<L, G, R, TSEL>(p, sg * (32 / G) * L::NS, tab, threadIdx.x & 31)) {
+            comb_tile_tabg<L, R, G, PADU, TSEL>(p, sg, ch, ring, tab);
             return;
         }
     }
