@@ -89,7 +89,7 @@ typedef struct ap_dot {
 
 /* How a plot call is carried out (kernel variant and tiling); informational. */
 typedef struct ap_plan {
-    int32_t lane_bits;        /* 8 or 16: bits per seaweed key lane */
+    int32_t lane_bits;        /* 8, 10 or 16: bits per seaweed key lane */
     int32_t strips_per_reg;   /* strips held side by side in one 32-bit register */
     int32_t rows_per_lane;    /* comb rows each thread holds (compile-time) */
     int32_t lanes_per_strip;  /* threads that split one strip's rows */
@@ -98,6 +98,10 @@ typedef struct ap_plan {
     int64_t tiles;            /* strip groups x column chunks */
     int64_t physical_cells;   /* comb cell updates, warm-up and padding included */
     int64_t logical_cells;    /* (m - w)(n - w) w: window pairs times window length */
+    int32_t tables;           /* match tables, taken by warps whose x letters have at
+                                 most four values: 0 none; 1 one thread per strip
+                                 group; 2, 3 shared by the threads of a strip group,
+                                 their row split rounded down (2) or up (3) */
 } ap_plan;
 
 /* Library version string. */

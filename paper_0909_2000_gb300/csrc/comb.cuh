@@ -95,7 +95,7 @@ struct CombParams {
     int64_t step;       // x offset between consecutive plot rows (vertical step h)
     int32_t warp_words; // shared-memory words per warp of a plain launch
     uint32_t scale;     // plot values are scale x the comb's values (gcd of the scores)
-    int32_t tab;        // 1: the aligned row split of the G > 1 table path fits (tabg_split_ok)
+    int32_t tab;        // G > 1 tables: the row split's rounding mode (tabg_split_mode), 0 for none
     uint32_t *dbg;      // debug builds: violation bits of the bounds checks (device), else null
 };
 
@@ -949,7 +949,11 @@ __host__ __device__ constexpr bool has_tables(int key_bits, int groups, int nu, 
 // Columns of each step whose right output is formed on the FMA pipe.  With OR
 // masks one of the two was best (62.2 ms against 65.3 ms for none and 65.9 ms
 // for both); with selectors, whose h + 0x80.. already runs on the FMA pipe,
-// none (59.3 ms against 65.5 ms for one and 71.2 ms for both).
+// none (59.3 ms against 65.5 ms for one and 71.2 ms for both).  Finer mixes
+// lost as well: the FMA right output on every third, fourth or sixth cell
+// 62.0, 61.8 and 60.8 ms; every third cell on the ALU pipe alone (t by one
+// three-input add) and the others wholly on the FMA pipe 62.6 ms.  The fewest
+// issued instructions win, not the balance of the two pipes.
 #define AP_TAB_HNF 0
 #endif
 
@@ -1285,7 +1289,8 @@ __host__ __device__ constexpr int tabg_words(int ns, int g, int r)
 
 __host__ __device__ constexpr bool has_tables_g(int key_bits, int groups, int nu, bool xrows)
 {
-    return nu == 1 && !xrows && groups > 1 && (key_bits == 8 || key_bits == 9 || key_bits == 15);
+    return nu == 1 && !xrows && groups > 1 &&
+           (key_bits == 7 || key_bits == 8 || key_bits == 9 || key_bits == 15);
 }
 
 // Strips per register of a lane width (8, 10 or 16 bits).
@@ -1314,21 +1319,31 @@ __host__ __device__ constexpr uint32_t tab_nomatch()
     return SEL ? (L::BITS == 8 ? 0xBA98u : 0xBB99u) : (L::FULL ? 0u : L::MSB);
 }
 
-// First row of thread g's share (g = G: the window w).
-__host__ __device__ inline int tabg_ub(int w, int G, int rpl, int g)
+// First row of thread g's share (g = G: the window w): g w / G rounded down
+// (mode 1) or up (mode 2) to whole table loads of rpl rows.
+__host__ __device__ inline int tabg_ub(int w, int G, int rpl, int g, int mode)
 {
-    return g >= G ? w : (g * w / G) / rpl * rpl;
+    if (g >= G) return w;
+    return mode == 2 ? ((g * w + G - 1) / G + rpl - 1) / rpl * rpl : (g * w / G) / rpl * rpl;
 }
 
-// The aligned split fits: every share has at most R rows and at least
-// R - PADU of them are real.
-__host__ __device__ inline bool tabg_split_ok(int w, int G, int R, int rpl, int padu)
+// The aligned split of a mode fits: every share has at most R rows and at
+// least R - PADU of them are real.
+__host__ __device__ inline bool tabg_split_ok(int w, int G, int R, int rpl, int padu, int mode)
 {
     for (int g = 0; g < G; ++g) {
-        const int n = tabg_ub(w, G, rpl, g + 1) - tabg_ub(w, G, rpl, g);
+        const int n = tabg_ub(w, G, rpl, g + 1, mode) - tabg_ub(w, G, rpl, g, mode);
         if (n > R || n < R - padu) return false;
     }
     return true;
+}
+
+// The split mode of a plan: 1 (rounded down) or 2 (rounded up) where one of
+// them fits, else 0 (no G > 1 tables).  Between them every default plan of
+// w = 121..512 fits; rounding down alone missed a third of 121..254.
+__host__ __device__ inline int tabg_split_mode(int w, int G, int R, int rpl, int padu)
+{
+    return tabg_split_ok(w, G, R, rpl, padu, 1) ? 1 : (tabg_split_ok(w, G, R, rpl, padu, 2) ? 2 : 0);
 }
 
 template <int RPL>
@@ -1392,7 +1407,7 @@ __device__ __forceinline__ bool build_tables_g(const CombParams &p, int64_t iw, 
     }
     __syncwarp();
     for (int g = 0; g < G; ++g) {
-        const int ub = tabg_ub(wk, G, RPL, g);
+        const int ub = tabg_ub(wk, G, RPL, g, p.tab);
         uint32_t *copy = tab + g * S;
         for (int q = lane; q < Q; q += 32) {
             uint32_t ch[NS];
@@ -1463,8 +1478,9 @@ __device__ __forceinline__ void cell_txs(uint32_t &h, uint32_t &v, uint32_t S, u
 }
 
 #ifndef AP_TABG_SEL
-// 1: the G > 1 tables of full 8-bit keys hold byte-permute selectors instead
-// of OR masks (see cell_txs): measured on the 100k DNA plot, w = 128, comb
+// 1: the G > 1 tables of 8-bit lanes (7-bit or full 8-bit keys) hold
+// byte-permute selectors instead of OR masks (see cell_txs): measured on the
+// 100k DNA plot with full keys, w = 128, comb
 // alone, 132.3 ms against 148.8 ms.  16-bit lanes keep OR masks (selectors:
 // 380.6 ms against 373.0 at w = 256), and 10-bit lanes, which spread their
 // compare bits with multiplies, too.
@@ -1473,7 +1489,8 @@ __device__ __forceinline__ void cell_txs(uint32_t &h, uint32_t &v, uint32_t S, u
 #ifndef AP_TABG_HNF
 // Right output of the second column of each step on the FMA pipe in the
 // G > 1 table path (16- and 10-bit lanes, whose key sums fit their lanes;
-// full 8-bit keys keep the logic form).
+// 8-bit lanes keep the logic form: full keys would carry, and 7-bit keys take
+// selectors, which lose to it as on one thread).
 #define AP_TABG_HNF 1
 #endif
 
@@ -1504,7 +1521,7 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
     const int64_t c0 = ch * p.chunk;
     const int64_t c1 = (c0 + p.chunk < p.cols) ? c0 + p.chunk : p.cols;
     const int wk = p.w;
-    const int nreal = tabg_ub(wk, G, RPL, g + 1) - tabg_ub(wk, G, RPL, g);
+    const int nreal = tabg_ub(wk, G, RPL, g + 1, p.tab) - tabg_ub(wk, G, RPL, g, p.tab);
 
     const uint32_t nomatch = tab_nomatch<L, SEL>();
     // padding rows never match: OR masks are ANDed with the no-match word;
@@ -1635,7 +1652,7 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
                     const uint32_t s0 = pi >= 0 ? ((X0[r] & kp) | (nomatch & ~kp)) : X0[r];
                     const uint32_t s1 = pi >= 0 ? ((X1[r] & kp) | (nomatch & ~kp)) : X1[r];
                     cell_txs<L>(h[k], va, s0, neg1, one, false);
-                    cell_txs<L>(h[k], vb, s1, neg1, one, AP_TABG_HNF != 0);
+                    cell_txs<L>(h[k], vb, s1, neg1, one, AP_TABG_HNF != 0 && L::BITS != 8);
                 } else {
                     cell_tx<L>(h[k], va, X0[r], kp, neg1, sph, spl);
                     cell_tx<L>(h[k], vb, X1[r], kp, neg1, sph, spl, AP_TABG_HNF != 0, one);
@@ -1663,8 +1680,8 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
 }
 
 // Variants with match tables (LCS: 7-bit keys on one thread per strip
-// group; full 8-bit keys or 16-bit lanes on G > 1 threads, where the plan
-// allows the aligned split) first try them: warps whose x characters take
+// group; 7-bit, full 8-bit, 9-bit keys or 16-bit lanes on G > 1 threads,
+// where the plan allows the aligned split) first try them: warps whose x characters take
 // at most kTabSyms values comb through the tables.
 template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
 __device__ __forceinline__ void comb_tile_dispatch(const CombParams &p, int64_t sg, int64_t ch,
@@ -1672,19 +1689,47 @@ __device__ __forceinline__ void comb_tile_dispatch(const CombParams &p, int64_t 
 {
     constexpr bool FAST_OK = L::BITS == 8;
     constexpr bool TAB = L::BITS == 8 && !L::FULL && has_tables(7, G, NU, XR);
-    constexpr bool TABG = has_tables_g(L::BITS == 16 ? 15 : (L::BITS == 10 ? 9 : (L::FULL ? 8 : 0)), G, NU, XR);
+    constexpr bool TABG = has_tables_g(L::BITS == 16 ? 15 : (L::BITS == 10 ? 9 : (L::FULL ? 8 : 7)), G, NU, XR);
     if constexpr (TAB) {
         uint32_t *tab = ring + p.ring * (32 / G) + kOB * (32 / G + 1);
+        // The selector cells of the last PADU rows fold in the padding mask
+        // (one logic instruction a cell); w = R leaves no padding row and
+        // takes a tile without the fold.  Measured on the 100k DNA plot:
+        // w = 100 59.4 -> 56.7 ms, w = 16 16.2 -> 14.9 ms.  A second tile
+        // folding only the last 4 rows (R - w <= 4 in every plan of R >= 12)
+        // gained at most 1% at w = 97 and 117, and the code then generated for
+        // the w = R tile ran 3-4% slower (w = 100: 58.3 or 59.1 ms).
         if (build_tables<R, AP_TAB_SEL != 0>(p, sg * 128, tab, threadIdx.x & 31)) {
-            comb_tile_tab<R, PADU, AP_TAB_CPS, AP_TAB_HNF, AP_TAB_SEL != 0>(p, sg, ch, ring, tab);
+            if (p.w == R)
+                comb_tile_tab<R, 0, AP_TAB_CPS, AP_TAB_HNF, AP_TAB_SEL != 0>(p, sg, ch, ring, tab);
+            else
+                comb_tile_tab<R, PADU, AP_TAB_CPS, AP_TAB_HNF, AP_TAB_SEL != 0>(p, sg, ch, ring, tab);
             return;
         }
     }
     if constexpr (TABG) {
         uint32_t *tab = ring + p.ring * (32 / G) + kOB * (32 / G + 1);
-        constexpr bool TSEL = AP_TABG_SEL != 0 && L::FULL;
+        constexpr bool TSEL = AP_TABG_SEL != 0 && L::BITS == 8;
         if (p.tab && build_tables_g<L, G, R, TSEL>(p, sg * (32 / G) * L::NS, tab, threadIdx.x & 31)) {
-            comb_tile_tabg<L, R, G, PADU, TSEL>(p, sg, ch, ring, tab);
+            if constexpr (TSEL) {
+                // as on one thread: the padding fold spans the most padding
+                // rows any thread of the group holds (0, up to 4, or PADU)
+                constexpr int RPL = tabg_rpl(L::NS);
+                int npad = 0;
+                for (int q = 0; q < G; ++q) {
+                    const int n = tabg_ub(p.w, G, RPL, q + 1, p.tab) - tabg_ub(p.w, G, RPL, q, p.tab);
+                    npad = R - n > npad ? R - n : npad;
+                }
+                constexpr int NP4 = PADU < 4 ? PADU : 4;
+                if (npad == 0)
+                    comb_tile_tabg<L, R, G, 0, TSEL>(p, sg, ch, ring, tab);
+                else if (npad <= NP4)
+                    comb_tile_tabg<L, R, G, NP4, TSEL>(p, sg, ch, ring, tab);
+                else
+                    comb_tile_tabg<L, R, G, PADU, TSEL>(p, sg, ch, ring, tab);
+            } else {
+                comb_tile_tabg<L, R, G, PADU, TSEL>(p, sg, ch, ring, tab);
+            }
             return;
         }
     }
@@ -1694,9 +1739,26 @@ __device__ __forceinline__ void comb_tile_dispatch(const CombParams &p, int64_t 
         comb_tile<L, R, G, NU, MU, PADU, XR, false>(p, sg, ch, ring);
 }
 
+// Resident blocks per SM asked of the compiler.  Three (168 registers a
+// thread) where the shared memory allows them and the registers fit without
+// spills (LCS, not the vertical-step layout): full 8-bit keys on 4 threads up
+// to 60 rows (100k DNA plot, w = 200: 227 ms at 255 registers and two
+// blocks, 213 ms at three) and 7-bit keys on 2 threads up to 52 rows (w = 100
+// on request: 84 ms against 74 ms).  Elsewhere the compiler keeps its own
+// budget: capped at 168 registers, w = 256 in 16-bit lanes went from 373 to
+// 402 ms while the shared memory still held two blocks.
+template <class L, int R, int G, int NU, bool XR>
+__host__ __device__ constexpr int comb_min_blocks()
+{
+    return NU == 1 && !XR &&
+                   ((L::BITS == 8 && L::FULL && G == 4 && R <= 64) || (L::BITS == 8 && !L::FULL && G == 2 && R <= 52))
+               ? 3
+               : AP_MIN_BLOCKS;
+}
+
 // Plain launch: one warp per tile; tiles are numbered strip group fastest.
 template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, AP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, (comb_min_blocks<L, R, G, NU, XR>()))
 comb_kernel(CombParams p)
 {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -1727,7 +1789,7 @@ struct BatchParams {
 // list until it is exhausted.  Each tile is combed exactly as a plain launch
 // combs it, so results are bit-identical to one call per job.
 template <class L, int R, int G, int NU, int MU, int PADU, bool XR>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, AP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, (comb_min_blocks<L, R, G, NU, XR>()))
 comb_batch_kernel(BatchParams b)
 {
     extern __shared__ __align__(16) uint32_t smem[];

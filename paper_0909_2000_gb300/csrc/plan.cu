@@ -339,10 +339,18 @@ void fill_params(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y, 
     p->step = pl.step;
     p->warp_words = pl.warp_words;
     p->scale = (uint32_t)pl.scale;
-    const Variant *v = pl.v;
-    p->tab = has_tables_g(v->key_bits, v->groups, v->nu, v->xrows != 0) &&
-             tabg_split_ok(pl.w, v->groups, v->rows, tabg_rpl(lane_strips(v->lane_bits)), v->padu);
+    const int t = plan_tables(pl);
+    p->tab = t >= 2 ? t - 1 : 0;
     p->dbg = debug_flags();
+}
+
+int plan_tables(const Plan &pl)
+{
+    const Variant *v = pl.v;
+    if (has_tables(v->key_bits, v->groups, v->nu, v->xrows != 0)) return 1;
+    if (!has_tables_g(v->key_bits, v->groups, v->nu, v->xrows != 0)) return 0;
+    const int mode = tabg_split_mode(pl.w, v->groups, v->rows, tabg_rpl(lane_strips(v->lane_bits)), v->padu);
+    return mode ? 1 + mode : 0;
 }
 
 cudaError_t raise_smem_limit(const void *fn)

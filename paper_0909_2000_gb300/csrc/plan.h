@@ -55,4 +55,9 @@ cudaError_t launch_comb(const Plan &pl, const uint8_t *x, int64_t m, const uint8
 // Physical comb cell updates for a plan (warm-up and padding included).
 int64_t physical_cells(const Plan &pl);
 
+// Match tables of a plan (used by warps whose x letters take at most four
+// values): 0 none; 1 one thread per strip group; 2, 3 shared by G > 1
+// threads, the row split rounded down (2) or up (3).
+int plan_tables(const Plan &pl);
+
 }  // namespace ap

@@ -206,3 +206,32 @@ def test_requested_layouts_keep_padding_within_the_masked_rows(w, bits, g):
         ap.set_lanes_per_strip(0)
     G, R = pl["lanes_per_strip"], pl["rows_per_lane"]
     assert R * G >= w and R - w // G <= 8, pl
+
+
+@pytest.mark.parametrize("bits", [0, 8, 10, 16])
+@pytest.mark.parametrize("g", [0, 1, 2, 4, 8])
+def test_every_lcs_layout_has_match_tables(bits, g):
+    """Every LCS plan, automatic or requested, has match tables for warps of
+    at most four letters: on one thread (7-bit keys), or shared by the G
+    threads of a strip group with g w / G rounded down (2) or up (3) to whole
+    table loads (4, 2, 1 rows for 8-, 16-, 10-bit lanes) as the first row of
+    thread g; each thread's share then holds at most its R rows and at most
+    8 (the masked padding rows) fewer."""
+    try:
+        ap.set_lane_bits(bits)
+        ap.set_lanes_per_strip(g)
+        plans = {w: ap.plot_plan(w + 700, w + 600, w) for w in range(1, 513)}
+    finally:
+        ap.set_lane_bits(0)
+        ap.set_lanes_per_strip(0)
+    for w, pl in plans.items():
+        G, R, t = pl["lanes_per_strip"], pl["rows_per_lane"], pl["tables"]
+        if G == 1:
+            assert t == 1 and pl["lane_bits"] == 8, (w, pl)
+            continue
+        assert t in (2, 3), (w, pl)
+        rpl = {8: 4, 16: 2, 10: 1}[pl["lane_bits"]]
+        ub = [(-(-(k * w) // G) + rpl - 1) // rpl * rpl if t == 3 else (k * w // G) // rpl * rpl
+              for k in range(G)] + [w]
+        shares = [ub[k + 1] - ub[k] for k in range(G)]
+        assert all(R - 8 <= s <= R for s in shares), (w, pl, shares)

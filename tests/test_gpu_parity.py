@@ -166,6 +166,38 @@ def test_lane_formats_at_shared_windows(cuda_lib, bits, g, w, alph):
     assert got.shape == o.shape and np.array_equal(got, o), np.argwhere(got != o)[:4].tolist()
 
 
+# Match tables shared by the threads of a strip group, on DNA (four letters):
+# windows whose row split must be rounded up (plan "tables" 3) in full 8-bit
+# keys on 2 and 4 threads and 16-bit lanes on 2 and 8, and 7-bit keys on 2
+# and 4 threads (requested layouts; one thread is their default).  In 8-bit
+# lanes the padding fold spans 0 (w = 128), up to 4 (126, 133, 207, 254, 100,
+# 63, 58, 21) or 8 rows (20 on 2 threads, 10 on 4), by the most padding rows
+# one thread of the group holds.
+SPLIT_CASES = [(0, 0, 126, 3), (0, 0, 133, 3), (0, 0, 207, 3), (0, 0, 254, 3), (0, 0, 505, 3),
+               (8, 2, 100, 2), (8, 2, 63, 3), (8, 4, 58, 3), (8, 4, 21, 3), (16, 2, 127, 3),
+               (0, 0, 128, 2), (8, 2, 20, 2), (8, 4, 10, 2)]
+
+
+@pytest.mark.parametrize("bits,g,w,mode", SPLIT_CASES)
+def test_shared_tables_row_splits(cuda_lib, bits, g, w, mode):
+    ap = cuda_lib
+    seed = 7000 + bits * 100 + g * 10 + w
+    x = synth.alphabet_string(seed, 1, w + 260, synth.DNA)
+    y = synth.alphabet_string(seed, 2, w + 333, synth.DNA)
+    y, _ = synth.plant(x, y, 1, 150, seed, 3, synth.DNA, 0.1, 0.05)
+    o = oracle.plot(x, y, w)
+    try:
+        ap.set_lane_bits(bits)
+        ap.set_lanes_per_strip(g)
+        pl = ap.plot_plan(len(x), len(y), w)
+        assert pl["tables"] == mode and pl["lanes_per_strip"] > 1, pl
+        got = gpu_plot(ap, x, y, w, (1, 0, 0), torch.int16) & 0xFFFF
+    finally:
+        ap.set_lane_bits(0)
+        ap.set_lanes_per_strip(0)
+    assert got.shape == o.shape and np.array_equal(got, o), np.argwhere(got != o)[:4].tolist()
+
+
 @pytest.mark.parametrize("w,scores", [(9, (1, 0, 0)), (100, (1, 0, 0)), (150, (1, 0, 0)),
                                       (300, (1, 0, 0)), (20, (2, 1, 0)), (90, (2, 1, 0)),
                                       (140, (2, 1, 0))])
