@@ -56,8 +56,9 @@ def _variants():
         v.append(("U10Lanes", 9, 10, r, 8, 1, 0, 8))
 
     # LCS, 15-bit keys in 16-bit lanes, rows split over 2, 4 or 8 threads: w <= 512
+    # (4 threads up to 96 rows: w <= 384)
     for g in (2, 4, 8):
-        for r in range(16, 65, 8):
+        for r in range(16, (97 if g == 4 else 65), 8):
             v.append(("U16Lanes", 15, 16, r, g, 1, 0, 8))
     # {2,1,0}, 15-bit pair keys, 8 threads: w <= 256
     for rp in range(16, 33, 4):
@@ -98,13 +99,14 @@ NUNITS = 12   # translation units for the instantiations
 # The bounds-checked debug build (AP_DEBUG_BOUNDS) compiles a few variants
 # only, one of each kind of kernel the tests exercise: LCS in 7-bit keys on
 # one thread (w 13..16 and 97..100) and two threads, full 8-bit keys on two
-# threads, 16-bit lanes on four, 10-bit lanes on four; {2,1,0} on one thread
+# threads, 16-bit lanes on four (64 and 80 rows), 10-bit lanes on four; {2,1,0} on one thread
 # and in 16-bit lanes; {3,1,0}; the vertical-step layout.
 DEBUG_BUILD = os.path.join(HERE, "_build_debug")
 DEBUG_LIB = os.path.join(HERE, "libalnplot_debug.so")
 DEBUG_KINDS = {("U8Lanes", 16, 1, 1, 0, False), ("U8Lanes", 100, 1, 1, 0, False),
                ("U8Lanes", 40, 2, 1, 0, False), ("U8FLanes", 64, 2, 1, 0, False),
-               ("U16Lanes", 64, 4, 1, 0, False), ("U10Lanes", 75, 4, 1, 0, False),
+               ("U16Lanes", 64, 4, 1, 0, False), ("U16Lanes", 80, 4, 1, 0, False),
+               ("U10Lanes", 75, 4, 1, 0, False),
                ("U8Lanes", 48, 1, 2, 1, False), ("U16Lanes", 64, 8, 2, 1, False),
                ("U8Lanes", 24, 1, 3, 1, False), ("U8Lanes", 16, 1, 1, 0, True)}
 

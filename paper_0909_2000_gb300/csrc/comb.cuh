@@ -203,6 +203,22 @@ __device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
     return r;
 }
 
+// Per-half unsigned maximum and minimum of two 16-bit lane pairs (one
+// instruction each on sm_90 and later).
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
 // Full-width unsigned a >= b in every lane, as the lane's top bit (other bits
 // are junk): compare the low bits with the top bit forced on a and off b (no
 // borrow between lanes), then let the top bits decide where they differ.
@@ -1303,9 +1319,22 @@ __host__ __device__ constexpr int lane_strips(int lane_bits)
 // match: 0 for full 8-bit keys, the lane's top bit otherwise) or
 // byte-permute selectors (match: bytes of the all-ones constant; no match:
 // the lane's sign spread over its bytes).
+#ifndef AP_TABG_MM
+// 1: the G > 1 tables of 16-bit lanes hold the match bit (0x8000 in match
+// lanes, 0 otherwise) for the min/max cell (cell_tmm).
+#define AP_TABG_MM 1
+#endif
+
+template <class L>
+__host__ __device__ constexpr bool tab_minmax()
+{
+    return AP_TABG_MM != 0 && L::BITS == 16;
+}
+
 template <class L, bool SEL>
 __host__ __device__ constexpr uint32_t tab_lane_word(bool hit, int b)
 {
+    if (tab_minmax<L>()) return hit ? (0x8000u << (16 * b)) : 0u;
     if (!SEL) return hit ? (L::MASK << (L::BITS * b)) : (L::FULL ? 0u : (L::MSB & (L::MASK << (L::BITS * b))));
     if (L::BITS == 8) return (uint32_t)(hit ? 4 + b : 8 + b) << (4 * b);
     // 16-bit lane b: bytes 2b, 2b + 1
@@ -1316,7 +1345,7 @@ __host__ __device__ constexpr uint32_t tab_lane_word(bool hit, int b)
 template <class L, bool SEL>
 __host__ __device__ constexpr uint32_t tab_nomatch()
 {
-    return SEL ? (L::BITS == 8 ? 0xBA98u : 0xBB99u) : (L::FULL ? 0u : L::MSB);
+    return tab_minmax<L>() ? 0u : (SEL ? (L::BITS == 8 ? 0xBA98u : 0xBB99u) : (L::FULL ? 0u : L::MSB));
 }
 
 // First row of thread g's share (g = G: the window w): g w / G rounded down
@@ -1475,6 +1504,21 @@ __device__ __forceinline__ void cell_txs(uint32_t &h, uint32_t &v, uint32_t S, u
     if (FMA_HN && !L::FULL) h = mad_lo(vn, neg1, mad_lo(h, one, v));
     else h = h ^ v ^ vn;
     v = vn;
+}
+
+// One comb cell of 16-bit lanes with a min/max table word X (0x8000 in match
+// lanes; X & pk is 0 in padding rows).  In a match lane h + 0x8000 exceeds
+// every key, so the maximum is h + 0x8000 (bottom h once X is taken off)
+// and the minimum v; elsewhere bottom = max(h, v) and right = min(h, v): the
+// same swap as cell_tx, in two multiply-adds and two 16x2 min/max.
+__device__ __forceinline__ void cell_tmm(uint32_t &h, uint32_t &v, uint32_t X, uint32_t pk,
+                                         uint32_t one, uint32_t neg1)
+{
+    const uint32_t xm = X & pk;
+    const uint32_t hc = mad_lo(h, one, xm);
+    const uint32_t b = max_u16x2(hc, v);
+    h = min_u16x2(hc, v);
+    v = mad_lo(xm, neg1, b);
 }
 
 #ifndef AP_TABG_SEL
@@ -1653,6 +1697,9 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
                     const uint32_t s1 = pi >= 0 ? ((X1[r] & kp) | (nomatch & ~kp)) : X1[r];
                     cell_txs<L>(h[k], va, s0, neg1, one, false);
                     cell_txs<L>(h[k], vb, s1, neg1, one, AP_TABG_HNF != 0 && L::BITS != 8);
+                } else if constexpr (tab_minmax<L>()) {
+                    cell_tmm(h[k], va, X0[r], kp, one, neg1);
+                    cell_tmm(h[k], vb, X1[r], kp, one, neg1);
                 } else {
                     cell_tx<L>(h[k], va, X0[r], kp, neg1, sph, spl);
                     cell_tx<L>(h[k], vb, X1[r], kp, neg1, sph, spl, AP_TABG_HNF != 0, one);
@@ -1741,17 +1788,19 @@ __device__ __forceinline__ void comb_tile_dispatch(const CombParams &p, int64_t 
 
 // Resident blocks per SM asked of the compiler.  Three (168 registers a
 // thread) where the shared memory allows them and the registers fit without
-// spills (LCS, not the vertical-step layout): full 8-bit keys on 4 threads up
-// to 60 rows (100k DNA plot, w = 200: 227 ms at 255 registers and two
-// blocks, 213 ms at three) and 7-bit keys on 2 threads up to 52 rows (w = 100
-// on request: 84 ms against 74 ms).  Elsewhere the compiler keeps its own
-// budget: capped at 168 registers, w = 256 in 16-bit lanes went from 373 to
-// 402 ms while the shared memory still held two blocks.
+// spills (LCS, not the vertical-step layout): full 8-bit keys on 4 threads
+// (100k DNA plot, w = 200: 227 ms at 255 registers and two blocks, 213 ms at
+// three), 16-bit lanes on 4 threads up to 64 rows (w = 256: 311 -> 285 ms;
+// a few bytes spill at 64 rows) and 7-bit keys on 2 threads up to 52 rows
+// (w = 100 on request: 84 ms against 74 ms).  Elsewhere the compiler keeps
+// its own budget: where the shared memory holds two blocks anyway (w = 128
+// on 2 threads) the cap only costs.
 template <class L, int R, int G, int NU, bool XR>
 __host__ __device__ constexpr int comb_min_blocks()
 {
     return NU == 1 && !XR &&
-                   ((L::BITS == 8 && L::FULL && G == 4 && R <= 64) || (L::BITS == 8 && !L::FULL && G == 2 && R <= 52))
+                   ((L::BITS == 16 && G == 4 && R <= 64) || (L::BITS == 8 && L::FULL && G == 4 && R <= 64) ||
+                    (L::BITS == 8 && !L::FULL && G == 2 && R <= 52))
                ? 3
                : AP_MIN_BLOCKS;
 }

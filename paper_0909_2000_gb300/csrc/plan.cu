@@ -53,7 +53,7 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
     const bool score = nu > 1;
     const int xrows = step > 1 ? 1 : 0;
     // key_bits: 7 (w <= 120), 8 (LCS, w <= 254: values fit a byte), 9 (LCS, 10-bit
-    // lanes, 256 < w <= 480), else 15.
+    // lanes on request, 120 < w <= 480), else 15.
     int kbits = 0, rows = 0, groups = 0;
     auto rows_for = [&](int g, int unit, int lo, int hi) -> bool {
         // rows per thread for g threads: units (rows or pairs) rounded up to a
@@ -96,10 +96,10 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
         if (want16) {
             kbits = 15;
             if (want_groups == 2 || want_groups == 4 || want_groups == 8)
-                rows_for(want_groups, 8, 16, 64);
+                rows_for(want_groups, 8, 16, want_groups == 4 ? 96 : 64);
             if (!rows)
                 for (int g : {2, 4, 8})
-                    if (rows_for(g, 8, 16, 64)) break;
+                    if (rows_for(g, 8, 16, g == 4 ? 96 : 64)) break;
         } else if (want10) {
             kbits = 9;
             if (want_groups != 8) rows_for(4, 3, 33, 96);
@@ -109,25 +109,23 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
             if (want_groups == 2) rows_for(2, 4, 16, 60);
             else if (want_groups == 4) rows_for(4, 4, 8, 32);
             if (!rows) rows_for(1, 4, 8, 120);
-        } else if (w <= 254) {
+        } else if (w <= 240 || (want_lane_bits == 8 && w <= 254)) {
+            // full 8-bit keys; above w = 240 (64 rows on 4 threads) 16-bit
+            // lanes are faster: w = 254 285 ms against 339 ms
             kbits = 8;
             if (want_groups == 4 || !rows_for(2, 64, 64, 64)) rows_for(4, 4, 32, 64);
-        } else if (w > 256 && w <= 480) {
-            // 9-bit keys in 10-bit lanes, three strips per register.  Measured
-            // against 16-bit lanes on 100k DNA plots: w = 300: 536 vs 592 ms,
-            // w = 384: 701 vs 690 ms (16-bit lanes on 4 threads of 96 rows;
-            // on 8 threads, as built, 750 ms); at w = 256, where 16-bit lanes
-            // fit 4 threads of 64 rows exactly, 494 vs 472 ms, so w <= 256
-            // keeps 16-bit lanes.
-            kbits = 9;
-            if (want_groups == 8 || !rows_for(4, 3, 66, 96)) rows_for(8, 3, 33, 60);
         } else {
+            // 16-bit lanes (min/max cells): 4 threads up to 96 rows (w <= 384),
+            // then 8.  Measured against 9-bit keys in 10-bit lanes on 100k DNA
+            // plots: w = 272 326 vs 424 ms, w = 300 358 vs 451 ms, w = 384 407
+            // vs 564 ms, w = 448 (8 threads) 552 vs 757 ms; 10-bit lanes stay
+            // available on request.
             kbits = 15;
             if (want_groups == 2 || want_groups == 4 || want_groups == 8)
-                rows_for(want_groups, 8, 16, 64);
+                rows_for(want_groups, 8, 16, want_groups == 4 ? 96 : 64);
             if (!rows)
                 for (int g : {2, 4, 8})
-                    if (rows_for(g, 8, 16, 64)) break;
+                    if (rows_for(g, 8, 16, g == 4 ? 96 : 64)) break;
         }
     } else if (nu == 2 && mu == 1) {
         if (w <= 64) {
@@ -176,8 +174,12 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
     // Exit ring and key range.  7-bit keys: the ring has next_pow2(2w + 2)
     // slots (32..128) and keys stay below the ring size, so the kernel's exit
     // counting needs no branch; the new key cycles through [w, ring - 1].
-    // Full 8-bit keys: ring 256, keys in [w, 255].  15-bit keys: ring =
-    // next_pow2(w + 1), keys below 32768.
+    // Full 8-bit keys: ring 256, keys in [w, 255].  9- and 15-bit keys find
+    // exits by age: a valid exit at column c has age a < w and marks slot
+    // c - a, and the slot of c - w is expired before column c's exits are
+    // counted, so the live slots are the w columns c - w + 1 .. c and the
+    // ring needs next_pow2(w) slots (w = 512: 16 KB a warp less than
+    // next_pow2(w + 1), which had left room for one block per SM).
     if (v->key_bits == 7) {
         pl->ring = std::min(128, std::max(32, next_pow2(2 * w + 2)));
         pl->renorm = score ? (pl->ring - w) : (pl->ring - w) / 2;
@@ -186,10 +188,10 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
         pl->renorm = score ? (256 - w) : (256 - w) / 2;
     } else if (v->key_bits == 9) {
         // keys cycle through [w, 511]; exits are found by age, as for 15-bit keys
-        pl->ring = next_pow2(w + 1);
+        pl->ring = next_pow2(w);
         pl->renorm = (512 - w) / 2;
     } else {
-        pl->ring = next_pow2(w + 1);
+        pl->ring = next_pow2(w);
         pl->renorm = score ? (32768 - w) : (32768 - w) / 2;
     }
     const int nlanes = v->lane_bits == 8 ? 4 : (v->lane_bits == 10 ? 3 : 2);

@@ -70,7 +70,8 @@ def test_host_side_validation_without_gpu():
 
 
 @pytest.mark.parametrize("w,scores", [(1, ap.LCS), (16, ap.LCS), (100, ap.LCS), (120, ap.LCS),
-                                      (121, ap.LCS), (128, ap.LCS), (129, ap.LCS), (254, ap.LCS),
+                                      (121, ap.LCS), (128, ap.LCS), (129, ap.LCS), (240, ap.LCS),
+                                      (241, ap.LCS), (254, ap.LCS),
                                       (255, ap.LCS), (256, ap.LCS), (257, ap.LCS), (300, ap.LCS), (384, ap.LCS),
                                       (480, ap.LCS), (481, ap.LCS), (512, ap.LCS), (1, ap.SCORE),
                                       (64, ap.SCORE), (65, ap.SCORE), (120, ap.SCORE),
@@ -81,11 +82,11 @@ def test_every_supported_window_has_a_variant(w, scores):
     assert pl["comb_rows"] == rows
     assert pl["rows_per_lane"] * pl["lanes_per_strip"] >= rows
     assert pl["logical_cells"] == 1000 * 777 * w
-    # key width: 7-bit up to w = 120, then full 8-bit lanes up to 254 (LCS only,
-    # its values stay below 256), 10-bit lanes (LCS) for 256 < w <= 480, 16-bit
-    # lanes otherwise
+    # key width: 7-bit up to w = 120, then full 8-bit lanes up to 240 (LCS only;
+    # up to 254 on request), 16-bit lanes otherwise (10-bit lanes only on
+    # request)
     lcs = scores == ap.LCS
-    want = 8 if (w <= 120 or (w <= 254 and lcs)) else (10 if (256 < w <= 480 and lcs) else 16)
+    want = 8 if (w <= 120 or (w <= 240 and lcs)) else 16
     assert pl["lane_bits"] == want
     assert pl["strips_per_reg"] == {8: 4, 10: 3, 16: 2}[want]
     assert pl["physical_cells"] >= pl["logical_cells"] * (4 if scores == ap.SCORE else 1)

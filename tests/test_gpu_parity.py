@@ -60,7 +60,8 @@ CASES = [
     (600, 640, 200, b"AC", (2, 1, 0)),
     (600, 620, 254, b"ACGT", (2, 1, 0)),
     (620, 640, 255, b"ACGT", (2, 1, 0)),
-    # 10-bit lanes (three strips per register): 256 < w <= 480
+    # 16-bit lanes (min/max cells) on 4 threads of up to 96 rows: 256 < w <= 384,
+    # then 8 threads
     (600, 620, 257, b"ACGT", (1, 0, 0)),
     (700, 760, 300, b"ACGT", (1, 0, 0)),
     (640, 700, 384, b"AC", (1, 0, 0)),
@@ -141,7 +142,8 @@ def test_scaled_and_wide_score_schemes(cuda_lib, m, n, w, scores):
 # (table paths) and 20 letters (general paths).
 LANE_CASES = [(bits, g, w, alph) for bits, g, w in
               [(10, 4, 121), (10, 4, 128), (10, 4, 129), (10, 4, 200), (10, 4, 256), (10, 8, 250),
-               (16, 2, 126), (16, 4, 200), (16, 8, 254), (8, 2, 127), (8, 4, 201)]
+               (16, 2, 126), (16, 4, 200), (16, 8, 254), (8, 2, 127), (8, 4, 201),
+               (10, 4, 300), (10, 8, 480), (16, 8, 384)]
               for alph in (b"ACGT", b"ACDEFGHIKLMNPQRSTVWY")]
 
 
@@ -173,7 +175,7 @@ def test_lane_formats_at_shared_windows(cuda_lib, bits, g, w, alph):
 # lanes the padding fold spans 0 (w = 128), up to 4 (126, 133, 207, 254, 100,
 # 63, 58, 21) or 8 rows (20 on 2 threads, 10 on 4), by the most padding rows
 # one thread of the group holds.
-SPLIT_CASES = [(0, 0, 126, 3), (0, 0, 133, 3), (0, 0, 207, 3), (0, 0, 254, 3), (0, 0, 505, 3),
+SPLIT_CASES = [(0, 0, 126, 3), (0, 0, 133, 3), (0, 0, 207, 3), (8, 0, 254, 3), (0, 0, 505, 3),
                (8, 2, 100, 2), (8, 2, 63, 3), (8, 4, 58, 3), (8, 4, 21, 3), (16, 2, 127, 3),
                (0, 0, 128, 2), (8, 2, 20, 2), (8, 4, 10, 2)]
 
@@ -195,6 +197,19 @@ def test_shared_tables_row_splits(cuda_lib, bits, g, w, mode):
     finally:
         ap.set_lane_bits(0)
         ap.set_lanes_per_strip(0)
+    assert got.shape == o.shape and np.array_equal(got, o), np.argwhere(got != o)[:4].tolist()
+
+
+@pytest.mark.parametrize("w", [241, 250, 255])
+def test_16bit_lanes_into_byte_plots(cuda_lib, w):
+    """From w = 241 the default plan takes 16-bit lanes while the plot still
+    fits bytes: the uint8 plot equals the oracle's."""
+    ap = cuda_lib
+    x = synth.alphabet_string(w, 1, w + 300, synth.DNA)
+    y, _ = synth.plant(x, synth.alphabet_string(w, 2, w + 280, synth.DNA), 1, 150, w, 3, synth.DNA, 0.1, 0.05)
+    assert ap.plot_plan(len(x), len(y), w)["lane_bits"] == 16
+    got = gpu_plot(ap, x, y, w, (1, 0, 0), torch.uint8)
+    o = oracle.plot(x, y, w)
     assert got.shape == o.shape and np.array_equal(got, o), np.argwhere(got != o)[:4].tolist()
 
 
