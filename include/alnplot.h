@@ -63,13 +63,14 @@ typedef enum ap_status {
  *              scheme's plot; the reduced scheme with m/g >= 2 is combed as
  *              the LCS of blown-up windows, every character becoming x/g
  *              copies of '$' followed by m/g - x/g copies of itself.  Built:
- *              m/g <= 4 -- so {m, 0, 0} (m times the LCS, g = m) for any m,
- *              {2k, k, 0}, {3k, k, 0}, {3k, 2k, 0}, {4k, k, 0}, {4k, 3k, 0}.
- *              x w <= P <= m w.  Windows: as LCS for m/g = 1, as {2,1,0} for
- *              m/g = 2, up to 256 for m/g = 3, 4.
+ *              m/g <= 8 -- so {m, 0, 0} (m times the LCS, g = m) for any m,
+ *              {2k, k, 0}, {3k, k, 0}, {4k, 3k, 0}, {5k, 2k, 0}, {8k, 7k, 0}
+ *              and so on.  x w <= P <= m w.  Windows: as LCS for m/g = 1, as
+ *              {2,1,0} for m/g = 2, up to 256 for m/g = 3, 4, 192 for 5, 160
+ *              for 6, 128 for 7 and 8.
  * A scheme (a, b, c) with c < 0 maps to {a - 2c, b - 2c, 0} after scaling to
  * integers (and the plot value to S - 2wc).  Other normalised pairs
- * (m/g >= 5) return AP_E_UNSUPPORTED; so do plots whose largest value m w
+ * (m/g >= 9) return AP_E_UNSUPPORTED; so do plots whose largest value m w
  * exceeds 65535.
  */
 typedef struct ap_scores {

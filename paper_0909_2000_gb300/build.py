@@ -71,6 +71,11 @@ def _variants():
             v.append(("U8Lanes", 7, 8, nu * rp, 1, nu, mu, 8))
         for rp in range(4, 33, 4):
             v.append(("U16Lanes", 15, 16, nu * rp, 8, nu, mu, 4))
+    # nu = 5..8: one kernel per nu and row count for every mu (read at run
+    # time, mu = -1 here), 16-bit lanes on 8 threads, at most 128 rows a thread
+    for nu in (5, 6, 7, 8):
+        for rp in range(4, 128 // nu // 4 * 4 + 1, 4):
+            v.append(("U16Lanes", 15, 16, nu * rp, 8, nu, -1, 4))
     v = [t + (False,) for t in v]
     # vertical step h > 1 (one x word per unit): LCS w <= 120 and {2,1,0} w <= 120
     # in 8-bit lanes with 7-bit keys
@@ -100,7 +105,8 @@ NUNITS = 12   # translation units for the instantiations
 # only, one of each kind of kernel the tests exercise: LCS in 7-bit keys on
 # one thread (w 13..16 and 97..100) and two threads, full 8-bit keys on two
 # threads, 16-bit lanes on four (64 and 80 rows), 10-bit lanes on four; {2,1,0} on one thread
-# and in 16-bit lanes; {3,1,0}; the vertical-step layout.
+# and in 16-bit lanes; {3,1,0}; {5,x,0} (the '$' count read at run time); the
+# vertical-step layout.
 DEBUG_BUILD = os.path.join(HERE, "_build_debug")
 DEBUG_LIB = os.path.join(HERE, "libalnplot_debug.so")
 DEBUG_KINDS = {("U8Lanes", 16, 1, 1, 0, False), ("U8Lanes", 100, 1, 1, 0, False),
@@ -108,7 +114,8 @@ DEBUG_KINDS = {("U8Lanes", 16, 1, 1, 0, False), ("U8Lanes", 100, 1, 1, 0, False)
                ("U16Lanes", 64, 4, 1, 0, False), ("U16Lanes", 80, 4, 1, 0, False),
                ("U10Lanes", 75, 4, 1, 0, False),
                ("U8Lanes", 48, 1, 2, 1, False), ("U16Lanes", 64, 8, 2, 1, False),
-               ("U8Lanes", 24, 1, 3, 1, False), ("U8Lanes", 16, 1, 1, 0, True)}
+               ("U8Lanes", 24, 1, 3, 1, False), ("U16Lanes", 40, 8, 5, -1, False),
+               ("U8Lanes", 16, 1, 1, 0, True)}
 
 
 def _debug_variants():

@@ -66,9 +66,9 @@ ap_status score_mode(const ap_scores *sc, int *nu, int *mu, int *scale)
     }
     const int g = a;                                     // gcd(match, mismatch)
     const int rn = sc->match / g, rm = sc->mismatch / g;
-    if (rn > 4 || (int64_t)sc->match > 65535)
+    if (rn > 8 || (int64_t)sc->match > 65535)
         return fail(AP_E_UNSUPPORTED, "scores {%d,%d,0}: built are schemes whose reduced form "
-                    "{m/g, x/g, 0} (g = gcd(m, x)) has m/g <= 4", sc->match, sc->mismatch);
+                    "{m/g, x/g, 0} (g = gcd(m, x)) has m/g <= 8", sc->match, sc->mismatch);
     *nu = rn;
     *mu = rm;
     *scale = g;

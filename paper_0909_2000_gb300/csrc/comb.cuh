@@ -95,6 +95,7 @@ struct CombParams {
     int64_t step;       // x offset between consecutive plot rows (vertical step h)
     int32_t warp_words; // shared-memory words per warp of a plain launch
     uint32_t scale;     // plot values are scale x the comb's values (gcd of the scores)
+    int32_t mu;         // the blow-up's '$' count per character (variants built with MU = -1)
     int32_t tab;        // G > 1 tables: the row split's rounding mode (tabg_split_mode), 0 for none
     uint32_t *dbg;      // debug builds: violation bits of the bounds checks (device), else null
 };
@@ -546,7 +547,8 @@ __device__ __forceinline__ void flush_stage(const CombParams &p, const uint32_t 
 // G      threads per strip group (the strip's rows are split over them)
 // NU, MU blow-up of the score scheme {NU, MU, 0}: every character becomes
 //        MU '$' followed by NU - MU copies of itself (Section 2 for {2,1,0});
-//        NU = 1 is LCS
+//        NU = 1 is LCS; MU = -1 takes the '$' count from p.mu at run time
+//        (one kernel for every MU of a NU)
 // PADU   trailing units (rows for LCS, row groups of NU otherwise) of each
 //        thread that may be padding (never match)
 // XR     vertical step: plot row r is the x-window at r * step, so the NS
@@ -572,7 +574,7 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
     constexpr int SPW = NGRP * NS;                    // strips per warp
     constexpr int RP = R / NU;                        // x characters (units) per thread
     constexpr int NQ = XR ? RP : RP / L::RPW + 1;     // x words (aligned, or one per unit)
-    static_assert(NU >= 1 && MU >= 0 && MU < NU && (NU > 1 || MU == 0), "bad blow-up");
+    static_assert(NU >= 1 && MU >= -1 && MU < NU && (NU > 1 || MU == 0), "bad blow-up");
     static_assert(XR ? (R % NU == 0) : (R % (NU * L::RPW) == 0),
                   "R must fill whole units (vertical step) or whole x words");
     static_assert(PADU <= RP, "padding window larger than the lane");
@@ -849,6 +851,14 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
                     const int k = NU * q + rho;
 #pragma unroll
                     for (int c = 0; c < NU; ++c) {
+                        if constexpr (MU < 0) {
+                            // '$' rows and columns known at run time only
+                            // (uniform over the launch): select the cell's mask
+                            const bool rd = rho < p.mu, cd = c < p.mu;
+                            const uint32_t m = (rd && cd) ? pad : ((rd != cd) ? 0xFFFFFFFFu : mq);
+                            cell<L>(h[k], v[c], m, neg1, sph, spl);
+                            continue;
+                        }
                         const bool row_dollar = rho < MU, col_dollar = c < MU;
                         if (row_dollar && col_dollar) {
                             if (pi >= 0) {

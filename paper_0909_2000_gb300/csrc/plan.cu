@@ -139,7 +139,7 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
             kbits = 15;
             if (rows_for(8, 4, 16, 32)) rows *= 2;
         }
-    } else {
+    } else if (nu <= 4) {
         // {3 or 4, mu, 0}: 8-bit lanes while nu * w stays below 256 (w <= 32),
         // then 16-bit lanes on 8 threads (w <= 256).
         if (w <= 32) {
@@ -149,8 +149,14 @@ bool choose_variant(int w, int nu, int mu, int want_groups, int64_t step, Plan *
             kbits = 15;
             if (rows_for(8, 4, 4, 32)) rows *= nu;
         }
+    } else {
+        // {5..8, mu, 0}: 16-bit lanes on 8 threads, at most 128 rows a thread
+        // (w <= 192 for nu = 5, 160 for 6, 128 for 7 and 8); one kernel per
+        // nu and row count serves every mu (read at run time)
+        kbits = 15;
+        if (rows_for(8, 4, 4, 128 / nu / 4 * 4)) rows *= nu;
     }
-    const Variant *v = (rows > 0) ? find_variant(kbits, rows, groups, nu, mu, xrows) : nullptr;
+    const Variant *v = (rows > 0) ? find_variant(kbits, rows, groups, nu, nu >= 5 ? -1 : mu, xrows) : nullptr;
     if (v && !padding_ok(v, w)) v = nullptr;
     if (!v && (want_groups > 0 || want_lane_bits > 0))   // a request no variant serves:
         return choose_variant(w, nu, mu, 0, step, pl, why, 0);   // the automatic choice
@@ -341,6 +347,7 @@ void fill_params(const Plan &pl, const uint8_t *x, int64_t m, const uint8_t *y, 
     p->step = pl.step;
     p->warp_words = pl.warp_words;
     p->scale = (uint32_t)pl.scale;
+    p->mu = pl.mu;
     const int t = plan_tables(pl);
     p->tab = t >= 2 ? t - 1 : 0;
     p->dbg = debug_flags();

@@ -44,10 +44,13 @@ def test_host_side_validation_without_gpu():
         ap.plot_shape(10, 10, 0)
     assert e.value.status == ap.AP_E_INVAL
     with pytest.raises(ap.ApError) as e:
-        ap.plot_plan(100, 100, 10, (5, 1, 0))
+        ap.plot_plan(100, 100, 10, (9, 1, 0))      # reduced form {9,1,0}: not built
     assert e.value.status == ap.AP_E_UNSUPPORTED
     with pytest.raises(ap.ApError) as e:
         ap.plot_plan(100, 100, 10, (10, 3, 0))     # reduced form {10,3,0}: not built
+    assert e.value.status == ap.AP_E_UNSUPPORTED
+    with pytest.raises(ap.ApError) as e:
+        ap.plot_plan(1000, 1000, 193, (5, 1, 0))   # nu = 5: w <= 192
     assert e.value.status == ap.AP_E_UNSUPPORTED
     with pytest.raises(ap.ApError) as e:
         ap.plot_plan(1000, 1000, 257, (3, 1, 0))   # beyond the compiled windows
@@ -93,7 +96,8 @@ def test_every_supported_window_has_a_variant(w, scores):
 
 
 @pytest.mark.parametrize("nu,mu", [(3, 1), (3, 2), (4, 1), (4, 2), (4, 3), (2, 0), (7, 0), (6, 3), (6, 2),
-                                   (8, 6), (12, 3)])
+                                   (8, 6), (12, 3), (5, 1), (5, 4), (6, 1), (6, 5), (7, 2), (7, 6),
+                                   (8, 3), (8, 7), (10, 4), (16, 2)])
 @pytest.mark.parametrize("w", [1, 7, 32, 33, 64, 128, 200, 256])
 def test_blown_up_score_schemes_have_variants(nu, mu, w):
     """Schemes reduce by g = gcd(match, mismatch); the reduced blow-up is
@@ -101,7 +105,11 @@ def test_blown_up_score_schemes_have_variants(nu, mu, w):
     import math
     g = math.gcd(nu, mu)
     rn = nu // g
-    if rn == 1 and w > 512 or rn == 2 and w > 256:
+    # largest windows built: LCS 512, {2,1,0} 256, nu = 3, 4: 256, then
+    # 8 threads of at most 128 rows: 192 (nu = 5), 160 (6), 128 (7, 8)
+    if w > {1: 512, 2: 256, 3: 256, 4: 256, 5: 192, 6: 160, 7: 128, 8: 128}[rn]:
+        with pytest.raises(ap.ApError):
+            ap.plot_plan(w + 500, w + 300, w, (nu, mu, 0))
         return
     pl = ap.plot_plan(w + 500, w + 300, w, (nu, mu, 0))
     assert pl["comb_rows"] == rn * w

@@ -31,7 +31,8 @@ cases = [(300, 280, 16, (1, 0, 0), 1, 0, "dna", 0), (400, 420, 100, (1, 0, 0), 1
          (400, 380, 128, (1, 0, 0), 1, 0, "dna", 0), (500, 520, 256, (1, 0, 0), 1, 0, "dna", 0),
          (600, 620, 300, (1, 0, 0), 1, 0, "dna", 0), (600, 620, 300, (1, 0, 0), 1, 4, "dna", 10),
          (200, 210, 24, (2, 1, 0), 1, 0, "protein", 0), (500, 480, 250, (2, 1, 0), 1, 0, "dna", 0),
-         (150, 160, 8, (3, 1, 0), 1, 0, "dna", 0), (300, 280, 16, (1, 0, 0), 3, 0, "dna", 0)]
+         (150, 160, 8, (3, 1, 0), 1, 0, "dna", 0), (260, 240, 40, (5, 2, 0), 1, 0, "protein", 0),
+         (300, 280, 16, (1, 0, 0), 3, 0, "dna", 0)]
 out = []
 for k, (m, n, w, sc, step, g, alph, lb) in enumerate(cases):
     gen = synth.dna if alph == "dna" else synth.protein

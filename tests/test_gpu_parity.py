@@ -95,6 +95,13 @@ BLOWUP_CASES = [
     (120, 130, 5, (3, 1, 0)), (200, 170, 17, (3, 2, 0)), (300, 260, 32, (4, 1, 0)),
     (150, 222, 24, (4, 2, 0)), (190, 140, 9, (4, 3, 0)), (260, 300, 33, (3, 1, 0)),
     (300, 330, 70, (4, 3, 0)), (420, 400, 128, (3, 2, 0)), (350, 300, 100, (4, 1, 0)),
+    # nu = 5..8: one kernel per nu and row count, the '$' count read at run
+    # time; windows up to the largest built (192, 160, 128, 128)
+    (150, 140, 7, (5, 1, 0)), (260, 240, 40, (5, 2, 0)), (300, 320, 96, (5, 3, 0)),
+    (380, 400, 192, (5, 4, 0)), (200, 230, 33, (6, 1, 0)), (330, 300, 160, (6, 5, 0)),
+    (210, 190, 20, (7, 2, 0)), (260, 280, 64, (7, 4, 0)), (320, 300, 128, (7, 6, 0)),
+    (180, 200, 12, (8, 1, 0)), (300, 280, 100, (8, 5, 0)), (330, 340, 128, (8, 7, 0)),
+    (260, 250, 50, (10, 4, 0)),
 ]
 
 

@@ -96,7 +96,8 @@ def test_checksum_bands_add_up():
     assert total == parts
 
 
-@pytest.mark.parametrize("nu,mu", [(2, 1), (3, 1), (3, 2), (4, 1), (4, 2), (4, 3)])
+@pytest.mark.parametrize("nu,mu", [(2, 1), (3, 1), (3, 2), (4, 1), (4, 2), (4, 3), (5, 2), (6, 1), (7, 3),
+                                   (8, 5)])
 def test_blow_up_reduction_small_rational_scores(nu, mu):
     """Section 2: small rational scores reduce to LCS by blowing the strings
     up.  Reading: every character becomes mu '$' then nu - mu copies of
@@ -136,7 +137,7 @@ def test_bit_parallel_reference_equals_the_dynamic_programme(seed):
     rng = synth.below(seed, 1, 8, 1 << 30)
     alph = [b"AC", b"ACGT", bytes(range(256)), b"ACDEFGHIKLMNPQRSTVWY"][seed % 4]
     cases = [(1, 0, 63), (1, 0, 64), (1, 0, 65), (1, 0, 128), (1, 0, 129), (2, 1, 32), (2, 1, 33),
-             (2, 1, 64), (3, 2, 43), (4, 1, 16), (4, 3, 33), (1, 0, 300)]
+             (2, 1, 64), (3, 2, 43), (4, 1, 16), (4, 3, 33), (1, 0, 300), (5, 2, 20), (8, 3, 17)]
     for k, (nu, mu, w) in enumerate(cases):
         m = w + 1 + int(rng[k % 8]) % 60
         n = w + 1 + int(rng[(k + 3) % 8]) % 70
