@@ -245,6 +245,24 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def issue_probe(ap, index, sms):
+    """The integer issue rate behind the roofline's peak, measured by the
+    library's probe (ap_int_issue_probe): 32-bit lane operations per clock
+    and SM of three-input logic alone (ALU pipe), multiply-adds alone (FMA
+    pipe) and the two alternately, at the SM clock sampled meanwhile."""
+    kinds = {"alu_lop3": 0, "fma_imad": 1, "alu_and_fma": 2}
+    clocks = Clocks(index)
+    clocks.start()
+    rates = {k: ap.int_issue_probe(v, 1000000) for k, v in kinds.items()}
+    clk = clocks.stop()
+    mhz = clk["sm_mhz"] if clk else SM_MAX_MHZ
+    out = {k: r / (sms * mhz * 1e6) for k, r in rates.items()}
+    out.update({"unit": "int32 lane-ops/clk/SM", "sm_mhz": mhz,
+                "measured_peak_tops_at_max_clock": rates["alu_and_fma"] / mhz * SM_MAX_MHZ / 1e12,
+                "assumed_lanes_per_clk_per_sm": INT32_LANES_PER_SM_CLK})
+    return out
+
+
 def profile_traffic(kernel_tag):
     """dram bytes per launch from the committed ncu summary (profiles/traffic.md),
     if it was taken on the current kernel sources (else None)."""
@@ -889,6 +907,8 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
+    if world == 1:
+        line["roofline"]["peak_probe"] = issue_probe(ap, local, sms)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, k, dt, nth = oracle_rate(c, args.cpu_seconds)
         line["cpu_baseline"] = {"value": r, "unit": "cells/s", "cores": nth, "kind": "oracle",

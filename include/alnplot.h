@@ -343,6 +343,21 @@ ap_status ap_plot_checksum(const void *plot, int32_t elem_bytes, int64_t rows,
  */
 ap_status ap_debug_bounds(uint32_t *flags);
 
+/*
+ * Integer issue rate of the current device, the denominator of the comb
+ * kernel's roofline (not in the paper: a measurement aid).  A kernel of
+ * eight independent accumulators per thread, 64 warps an SM, updates each
+ * accumulator `iters` times from two others with one instruction:
+ *   kind 0  three-input logic (lop3)      -- the ALU pipe alone
+ *   kind 1  32-bit multiply-add (mad.lo)  -- the FMA pipe alone
+ *   kind 2  the two alternately           -- both pipes
+ * *lane_ops_per_s (host) receives the 32-bit lane operations per second of
+ * one timed launch (after one warm-up launch).  Synchronous; allocates
+ * nothing (its 16 KB result sink is a file-scope device array).
+ * AP_E_INVAL for kind outside 0..2, iters < 1 or a null pointer.
+ */
+ap_status ap_int_issue_probe(int32_t kind, int64_t iters, double *lane_ops_per_s);
+
 /* ------------------------------------------------------------------------
  * Batched plots: many independent (x, y, w) jobs, run as one CUDA graph of
  * persistent strip-comb kernels.  Not in the paper: it is the many-pairs

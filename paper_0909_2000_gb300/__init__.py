@@ -113,6 +113,7 @@ def _declare(lib):
         "ap_plot_checksum": [p, i32, i64, i64, i64, i32, u64p, p],
         "ap_plot_dots_noalloc": [p, i32, i64, i64, i64, i32, p, i64, i64p, p],
         "ap_debug_bounds": [ctypes.POINTER(ctypes.c_uint32)],
+        "ap_int_issue_probe": [i32, i64, ctypes.POINTER(ctypes.c_double)],
         "ap_batch_create": [ctypes.POINTER(ap_job), i32, ctypes.POINTER(ap_batch_options),
                             ctypes.POINTER(ctypes.c_void_p)],
         "ap_batch_run": [p, p],
@@ -476,6 +477,15 @@ def debug_bounds() -> int:
     f = ctypes.c_uint32()
     _check(load().ap_debug_bounds(ctypes.byref(f)))
     return f.value
+
+
+def int_issue_probe(kind: int, iters: int) -> float:
+    """32-bit lane operations per second of the integer issue probe (kind 0:
+    three-input logic, 1: multiply-add, 2: both alternately) on the current
+    device; see ap_int_issue_probe."""
+    r = ctypes.c_double()
+    _check(load().ap_int_issue_probe(int(kind), int(iters), ctypes.byref(r)))
+    return r.value
 
 
 def plot_checksum(plot, nbins: int, stream=None):

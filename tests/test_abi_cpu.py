@@ -244,3 +244,10 @@ def test_every_lcs_layout_has_match_tables(bits, g):
               for k in range(G)] + [w]
         shares = [ub[k + 1] - ub[k] for k in range(G)]
         assert all(R - 8 <= s <= R for s in shares), (w, pl, shares)
+
+
+def test_issue_probe_validates_before_touching_a_device():
+    for kind, iters in ((3, 10), (-1, 10), (0, 0)):
+        with pytest.raises(ap.ApError) as e:
+            ap.int_issue_probe(kind, iters)
+        assert e.value.status == ap.AP_E_INVAL
