@@ -60,7 +60,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lcs_dna_100k_w100",
                     choices=["lcs_dna_100k_w100", "lcs_dna_512_w16", "score_protein_20k_w64",
-                             "lcs_dna_20k_w100", "lcs_dna_20k_w256", "batch_dna_4096", "serve_dna_poisson",
+                             "lcs_dna_20k_w100", "lcs_dna_20k_w128", "lcs_dna_20k_w256", "batch_dna_4096",
+                             "serve_dna_poisson",
                              "score_dna_80k_w100_step5"])
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -87,6 +88,8 @@ def workload(name):
         return synth.dna_plot_512(0)
     if name == "lcs_dna_20k_w100":
         return synth.dna_plot_20k(0)
+    if name == "lcs_dna_20k_w128":
+        return synth.dna_plot_20k_w128(0)
     if name == "lcs_dna_20k_w256":
         return synth.dna_plot_20k_w256(0)
     return synth.protein_score_20k(0)

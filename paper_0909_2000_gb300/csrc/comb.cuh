@@ -308,9 +308,17 @@ __device__ __forceinline__ uint32_t mismatch_mask(uint32_t xw, uint32_t yb, uint
 #define AP_GEN_MM 1
 #endif
 
+#ifndef AP_GEN_HNF8
+// 1: full 8-bit keys in the general path form the right output as
+// (h + v) - bottom on the FMA pipe (exact, as in the table path): 40k
+// protein, w = 200, 47.1 -> 45.5 ms; 60k DNA with step 5, w = 200, 22.5 ->
+// 22.1 ms.
+#define AP_GEN_HNF8 1
+#endif
+
 template <class L>
 __device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t mm, uint32_t neg1,
-                                     uint32_t sph, uint32_t spl)
+                                     uint32_t sph, uint32_t spl, uint32_t one = 1u)
 {
     if constexpr (AP_GEN_MM != 0 && L::BITS == 16) {
         // 16-bit lanes: the key's top bit is free, so hc = h + 0x8000 in match
@@ -332,7 +340,8 @@ __device__ __forceinline__ void cell(uint32_t &h, uint32_t &v, uint32_t mm, uint
         M = spread<L>(t, sph, spl);
     }
     const uint32_t vn = (h & M) | (v & ~M);
-    h = h ^ v ^ vn;
+    if (L::FULL && AP_GEN_HNF8 != 0) h = mad_lo(vn, neg1, mad_lo(h, one, v));
+    else h = h ^ v ^ vn;
     v = vn;
 }
 
@@ -812,8 +821,8 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
                     m0 |= padm[pi < 0 ? 0 : pi];
                     m1 |= padm[pi < 0 ? 0 : pi];
                 }
-                cell<L>(h[k], va, m0, neg1, sph, spl);
-                cell<L>(h[k], vb, m1, neg1, sph, spl);
+                cell<L>(h[k], va, m0, neg1, sph, spl, one);
+                cell<L>(h[k], vb, m1, neg1, sph, spl, one);
             }
             vdown[0] = va;
             vdown[1] = vb;
@@ -856,13 +865,13 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
                             // (uniform over the launch): select the cell's mask
                             const bool rd = rho < p.mu, cd = c < p.mu;
                             const uint32_t m = (rd && cd) ? pad : ((rd != cd) ? 0xFFFFFFFFu : mq);
-                            cell<L>(h[k], v[c], m, neg1, sph, spl);
+                            cell<L>(h[k], v[c], m, neg1, sph, spl, one);
                             continue;
                         }
                         const bool row_dollar = rho < MU, col_dollar = c < MU;
                         if (row_dollar && col_dollar) {
                             if (pi >= 0) {
-                                cell<L>(h[k], v[c], pad, neg1, sph, spl);
+                                cell<L>(h[k], v[c], pad, neg1, sph, spl, one);
                             } else {
                                 const uint32_t tmp = h[k];
                                 h[k] = v[c];
@@ -871,7 +880,7 @@ __device__ __forceinline__ void comb_tile(const CombParams &p, int64_t sg, int64
                         } else if (row_dollar != col_dollar) {
                             cell_mismatch<L>(h[k], v[c], neg1, sph, spl);
                         } else {
-                            cell<L>(h[k], v[c], mq, neg1, sph, spl);
+                            cell<L>(h[k], v[c], mq, neg1, sph, spl, one);
                         }
                     }
                 }
@@ -1535,7 +1544,7 @@ __device__ __forceinline__ void cell_txs(uint32_t &h, uint32_t &v, uint32_t S, u
         M = prmt(t, 0xFFFFFFFFu, S);
     }
     const uint32_t vn = (h & M) | (v & ~M);
-    if (FMA_HN && !L::FULL) h = mad_lo(vn, neg1, mad_lo(h, one, v));
+    if (FMA_HN) h = mad_lo(vn, neg1, mad_lo(h, one, v));
     else h = h ^ v ^ vn;
     v = vn;
 }
@@ -1564,11 +1573,19 @@ __device__ __forceinline__ void cell_tmm(uint32_t &h, uint32_t &v, uint32_t X, u
 // compare bits with multiplies, too.
 #define AP_TABG_SEL 1
 #endif
+#ifndef AP_TABG_HNF8
+// Full 8-bit keys (their ALU pipe is the busy one, 87% against 9% for the
+// FMA pipe at w = 128): right outputs formed as (h + v) - bottom on the FMA
+// pipe in 0, 1 or 2 columns of each step.  The packed sum may carry between
+// lanes, but every lane's result lies in [0, 255], so the 32-bit result is
+// exact.  100k DNA plot, none / one / both: w = 128 124.6 / 121.7 / 119.5 ms,
+// w = 160 165.7 / 157.8 / 151.7 ms, w = 200 212.3 / 207.1 / 197.9 ms.
+#define AP_TABG_HNF8 2
+#endif
 #ifndef AP_TABG_HNF
 // Right output of the second column of each step on the FMA pipe in the
-// G > 1 table path (16- and 10-bit lanes, whose key sums fit their lanes;
-// 8-bit lanes keep the logic form: full keys would carry, and 7-bit keys take
-// selectors, which lose to it as on one thread).
+// G > 1 table path of 10-bit lanes (full 8-bit keys: AP_TABG_HNF8; 7-bit keys
+// keep the logic form, which wins with selectors as on one thread).
 #define AP_TABG_HNF 1
 #endif
 
@@ -1729,8 +1746,8 @@ __device__ __forceinline__ void comb_tile_tabg(const CombParams &p, int64_t sg, 
                 if (SEL) {
                     const uint32_t s0 = pi >= 0 ? ((X0[r] & kp) | (nomatch & ~kp)) : X0[r];
                     const uint32_t s1 = pi >= 0 ? ((X1[r] & kp) | (nomatch & ~kp)) : X1[r];
-                    cell_txs<L>(h[k], va, s0, neg1, one, false);
-                    cell_txs<L>(h[k], vb, s1, neg1, one, AP_TABG_HNF != 0 && L::BITS != 8);
+                    cell_txs<L>(h[k], va, s0, neg1, one, L::FULL && AP_TABG_HNF8 >= 2);
+                    cell_txs<L>(h[k], vb, s1, neg1, one, L::FULL ? AP_TABG_HNF8 >= 1 : (AP_TABG_HNF != 0 && L::BITS != 8));
                 } else if constexpr (tab_minmax<L>()) {
                     cell_tmm(h[k], va, X0[r], kp, one, neg1);
                     cell_tmm(h[k], vb, X1[r], kp, one, neg1);

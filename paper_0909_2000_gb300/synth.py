@@ -185,6 +185,15 @@ def dna_plot_20k(seed: int = 0) -> Pair:
     return c
 
 
+def dna_plot_20k_w128(seed: int = 0) -> Pair:
+    """The 20k DNA recipe at w = 128, a serving-mix window in full 8-bit keys
+    on two threads per strip group; dots >= ceil(0.8 w) = 103."""
+    c = dna_plot_100k(seed, 20_000, 20_000, 128, 4, 2000)
+    c.threshold = threshold_08(128)
+    c.name = "lcs_dna_20k_w128"
+    return c
+
+
 def dna_plot_20k_w256(seed: int = 0) -> Pair:
     """The 20k DNA recipe at w = 256, the serving mix's largest window: 16-bit
     keys and a uint16 plot (values reach 256); dots >= ceil(0.8 w) = 205."""
