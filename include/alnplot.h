@@ -103,6 +103,8 @@ typedef struct ap_plan {
                                  most four values: 0 none; 1 one thread per strip
                                  group; 2, 3 shared by the threads of a strip group,
                                  their row split rounded down (2) or up (3) */
+    int32_t smem_per_block;   /* dynamic shared memory of a block of the comb launch
+                                 (bytes): exit rings, output stages and tables */
 } ap_plan;
 
 /* Library version string. */

@@ -52,7 +52,8 @@ class ap_plan(ctypes.Structure):
                 ("rows_per_lane", ctypes.c_int32), ("lanes_per_strip", ctypes.c_int32),
                 ("comb_rows", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("tiles", ctypes.c_int64), ("physical_cells", ctypes.c_int64),
-                ("logical_cells", ctypes.c_int64), ("tables", ctypes.c_int32)]
+                ("logical_cells", ctypes.c_int64), ("tables", ctypes.c_int32),
+                ("smem_per_block", ctypes.c_int32)]
 
 
 class ap_job(ctypes.Structure):

@@ -239,6 +239,7 @@ ap_status ap_plot_plan(int64_t m, int64_t n, int32_t w, const ap_scores *scores,
     out->physical_cells = pl.ntiles ? physical_cells(pl) : 0;
     out->logical_cells = pl.rows * pl.cols * (int64_t)w;
     out->tables = plan_tables(pl);
+    out->smem_per_block = (int32_t)pl.smem;
     return AP_OK;
 }
 

@@ -251,3 +251,28 @@ def test_issue_probe_validates_before_touching_a_device():
         with pytest.raises(ap.ApError) as e:
             ap.int_issue_probe(kind, iters)
         assert e.value.status == ap.AP_E_INVAL
+
+
+@pytest.mark.parametrize("bits", [0, 8, 10, 16])
+@pytest.mark.parametrize("g", [0, 1, 2, 4, 8])
+def test_every_plan_fits_the_shared_memory_of_a_block(bits, g):
+    """Every plan, LCS or score, automatic or requested, asks a block for at
+    most 227 KB of shared memory (the sm_103a limit), so every launch can
+    run; the 100k bench plot fits two blocks per SM."""
+    plans = []
+    try:
+        ap.set_lane_bits(bits)
+        ap.set_lanes_per_strip(g)
+        for w in range(1, 513):
+            for sc in (ap.LCS, ap.SCORE, (3, 1, 0), (5, 2, 0), (8, 7, 0)):
+                try:
+                    plans.append((w, sc, ap.plot_plan(w + 700, w + 600, w, sc)))
+                except ap.ApError:
+                    pass
+    finally:
+        ap.set_lane_bits(0)
+        ap.set_lanes_per_strip(0)
+    assert plans
+    for w, sc, pl in plans:
+        assert 0 < pl["smem_per_block"] <= 227 * 1024, (w, sc, pl)
+    assert 2 * ap.plot_plan(100_000, 100_000, 100)["smem_per_block"] <= 228 * 1024
