@@ -881,7 +881,7 @@ def main():
     torch.cuda.empty_cache()
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(ap, c, scores, thr, dev, max(5, min(args.steps, 10)), dist, world, dev_dots)
+        e2e = measure_e2e(ap, c, scores, thr, dev, max(10, min(args.steps, 20)), dist, world, dev_dots)
 
     line = {
         "metric": "window-pair cells/sec (m*n*w/s)",
