@@ -157,7 +157,7 @@ ap_status ap_set_band_rows(int64_t rows);
  * Tuning: ask for a lane format of the LCS comb -- 8 (four strips per
  * register; windows up to 254), 10 (three strips; 121..480) or 16 bits (two
  * strips; any window up to 512) -- for later plot and dots calls in this
- * process; 0 restores the automatic choice.  Honoured where the format
+ * process; 0 restores the automatic choice (8 bits up to w = 240, then 16).  Honoured where the format
  * covers the window, else the automatic choice is used.  Results do not
  * depend on it.  Process-wide; AP_E_INVAL unless bits is 0, 8, 10 or 16.
  */
@@ -177,7 +177,7 @@ ap_status ap_set_lanes_per_strip(int32_t groups);
  *
  *   x       device, m bytes          y       device, n bytes
  *   w       window length, >= 1
- *   scores  host, {1,0,0} or {2,1,0} (see ap_scores)
+ *   scores  host, {1,0,0}, {2,1,0} or another built {m, x, 0} (see ap_scores)
  *   out     device, rows x ld elements, row-major; out[i*ld + j] = P[i][j]
  *   out_elem_bytes  1 (uint8) or 2 (uint16)
  *   ld      elements between consecutive rows, ld >= cols
@@ -185,9 +185,9 @@ ap_status ap_set_lanes_per_strip(int32_t groups);
  *
  * Errors: AP_E_INVAL for null pointers, w < 1, ld < cols, an element size
  * other than 1 or 2, or uint8 output when the largest possible value
- * (match * w) exceeds 255; AP_E_UNSUPPORTED for other
- * score schemes or w beyond the largest compiled comb height (LCS w <= 512,
- * {2,1,0} w <= 256);
+ * (match * w) exceeds 255; AP_E_UNSUPPORTED for score schemes not built
+ * or w beyond the largest compiled comb height (LCS w <= 512, {2,1,0} and
+ * m/g = 3, 4: w <= 256; m/g = 5: 192, 6: 160, 7 and 8: 128);
  * AP_E_CUDA if a launch fails.  If m <= w or n <= w the plot is empty:
  * nothing is written and AP_OK is returned.  Stream-ordered; allocates no
  * device memory.
